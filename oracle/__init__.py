@@ -1,0 +1,17 @@
+"""TEST INFRASTRUCTURE ONLY: the FP64 CPU oracle of the BLF-LS smoother.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import,
+call, link or execute anything in this package.  The product path (the CUDA library and its
+Python binding) never does, and this package never imports the product path.
+"""
+from .blfls_ref import (  # noqa: F401
+    blf,
+    blf_at,
+    blf_residuals,
+    blfls,
+    blfls_channel,
+    default_threads,
+    difference_otfs,
+    gradients,
+    solve_eq8,
+)
