@@ -1,0 +1,143 @@
+/*
+ * blfls.h -- C ABI of the GB300 (sm_103a) BLF-LS edge-preserving smoother.
+ *
+ * BLF-LS ("Embedding Bilateral Filter in Least Squares for Efficient Edge-preserving Image
+ * Smoothing", Section III-A) smooths an image f in two steps:
+ *   (1) the bilateral filter of Eq. 1 is run on the periodic forward-difference gradients
+ *       g_x = D_x f and g_y = D_y f (Section II-B operators), giving v_x, v_y;
+ *   (2) the least-squares problem of Eq. 7,
+ *           min_u  sum_s (u_s - f_s)^2 + lambda * sum_{*=x,y} (D_* u - v_*)_s^2,
+ *       is solved in closed form in the Fourier domain (Eq. 8) under periodic boundaries.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images are planar FP32, C channels of H x W, row-major, contiguous: element (c, y, x) is at
+ * img[(c * H + y) * W + x]; x runs along W.  Channels are smoothed independently.
+ * The bilateral window is the square of radius `radius` ((2r+1)^2 taps, centre included) with
+ * periodic wrap; spatial weight exp(-(dx^2+dy^2) / (2 sigma_s^2)), range weight
+ * exp(-(g_s - g_t)^2 / (2 sigma_r^2)) on the scalar field value (Eq. 1).  sigma_r = +INFINITY
+ * drops the range weight (a truncated Gaussian blur of the gradients).
+ * `iters` applies the whole smoother repeatedly: u_0 = img, u_k = BLFLS(u_{k-1}); iters = 0
+ * copies img to out.
+ *
+ * Argument rules (checked on the host; a violation returns BLFLS_EINVAL and launches nothing):
+ *   1 <= H, W <= BLFLS_MAX_DIM;  1 <= C <= BLFLS_MAX_CHANNELS;  radius >= 0 and
+ *   2*radius + 1 <= min(H, W);  sigma_s > 0;  sigma_r > 0 (may be +INFINITY);
+ *   lambda >= 0 and finite;  0 <= iters <= BLFLS_MAX_ITERS;  pointers non-NULL.
+ *
+ * Memory and streams: unless stated otherwise, image pointers are DEVICE pointers on the
+ * handle's device, owned by the caller, and work is enqueued asynchronously on `stream`
+ * (a cudaStream_t passed as void*; NULL is the legacy default stream).  The handle owns all
+ * scratch memory (FFT twiddle/permutation tables, the per-channel gradient residuals and
+ * spectrum) and grows it on demand, never beyond the budget given to blfls_create.
+ * out may equal img (in-place).  A handle must not be used from two threads at once, and two
+ * calls on the same handle must not run concurrently on different streams, because they share
+ * the handle's scratch memory (enqueue them on one stream).
+ *
+ * Errors: every call returns a blfls_status; nothing aborts or traps.  blfls_last_error()
+ * returns a human-readable message for the last failing call on the calling thread.
+ */
+#ifndef BLFLS_H
+#define BLFLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLFLS_MAX_DIM 8192
+#define BLFLS_MAX_CHANNELS 4
+#define BLFLS_MAX_ITERS 64
+
+typedef struct blfls_handle blfls_handle;
+
+typedef enum {
+    BLFLS_OK = 0,
+    BLFLS_EINVAL = -1,   /* an argument broke the rules above */
+    BLFLS_ENOMEM = -2,   /* the scratch memory would exceed the budget, or cudaMalloc failed */
+    BLFLS_ECUDA = -3,    /* a CUDA runtime call or a kernel launch failed */
+    BLFLS_ETIMEOUT = -4, /* a bounded device-side wait gave up (persistent work queue) */
+    BLFLS_EBUSY = -5     /* the serving queue is full */
+} blfls_status;
+
+/* Arithmetic of the bilateral window (step 1).  The Fourier solve is FP32 in every mode. */
+typedef enum {
+    BLFLS_FP32 = 0,  /* weights, products and sums in FP32 */
+    BLFLS_FP16W = 1, /* weights exp(.) and products w*g in FP16 (half2); sums in FP32 */
+    BLFLS_BF16W = 2  /* weights and products in BF16 (bfloat162); sums in FP32 */
+} blfls_precision;
+
+/* Create a handle on CUDA device `device`.  mem_budget_bytes caps the scratch memory the
+ * handle may allocate (0 = no cap).  tune_table_path names a tile-shape table written by the
+ * autotuner (blfls_autotune); NULL or a missing file selects the built-in defaults.
+ * On success *out receives the handle.  Errors: BLFLS_EINVAL (out NULL, bad device),
+ * BLFLS_ECUDA. */
+int blfls_create(blfls_handle **out, int device, size_t mem_budget_bytes,
+                 const char *tune_table_path);
+
+/* Free everything the handle owns, after waiting for its outstanding work.  NULL-safe. */
+void blfls_destroy(blfls_handle *h);
+
+/* Message of the last failing call on this thread ("" if none).  h may be NULL. */
+const char *blfls_last_error(blfls_handle *h);
+
+/* BLF-LS (Section III-A, Eqs. 1, 7, 8): out = BLFLS^iters(img).  Device pointers, async on
+ * `stream`.  `prec` is a blfls_precision. */
+int blfls_smooth(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                 float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
+                 void *stream);
+
+/* The same smoother on HOST buffers: copies img to the device, smooths, copies the result to
+ * out and waits for the stream.  img/out are host pointers (pinned memory copies fastest);
+ * the device copies live in the handle's scratch memory. */
+int blfls_smooth_host(blfls_handle *h, const float *img_host, float *out_host, int H, int W,
+                      int C, float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                      int prec, void *stream);
+
+/* Step 1 alone (Eq. 1 on the gradients of Section II-B): for every channel,
+ *   ex = f_BLF(D_x img) - D_x img,   ey = f_BLF(D_y img) - D_y img,
+ * i.e. how far the bilateral filter moves each gradient field.  ex, ey: device [C][H][W]. */
+int blfls_blf_residual(blfls_handle *h, const float *img, float *ex, float *ey, int H, int W,
+                       int C, float sigma_s, float sigma_r, int radius, int prec, void *stream);
+
+/* Step 2 alone (Eq. 8 in residual form): given guidance residuals e_* = v_* - D_* img,
+ *   out = img + (I + lambda L)^-1 lambda (D_x^T ex + D_y^T ey),   L = D_x^T D_x + D_y^T D_y,
+ * which equals Eq. 8 with v_* = D_* img + e_* (by linearity).  D^T are the backward
+ * differences of Section II-B.  All pointers device [C][H][W]; out may equal img. */
+int blfls_solve_residual(blfls_handle *h, const float *img, const float *ex, const float *ey,
+                         float *out, int H, int W, int C, float lambda, void *stream);
+
+/* One smoothing job of the batched and served forms. */
+typedef struct {
+    const float *img; /* device [C][H][W] */
+    float *out;       /* device [C][H][W]; may equal img */
+    int H, W, C;
+    float lambda, sigma_s, sigma_r;
+    int radius, iters;
+    int prec; /* blfls_precision */
+} blfls_job;
+
+/* Batched form: smooth n independent jobs of uneven sizes and parameters with one launch per
+ * pipeline phase (persistent kernels over a device work list).  Jobs are validated first; one
+ * bad job fails the call with BLFLS_EINVAL before anything is enqueued.  Results equal those
+ * of blfls_smooth on each job alone (same kernels, same arithmetic). */
+int blfls_smooth_batch(blfls_handle *h, const blfls_job *jobs, int n, void *stream);
+
+/* Kernel timing (no counterpart in the paper; measurement support for the benchmark).
+ * blfls_profile_begin pre-creates `max_events` CUDA events and starts recording an event pair
+ * around every kernel launch the handle makes, on the launch's own stream.  Stages:
+ * 0 = K1 bilateral residuals, 1 = K2 row FFTs, 2 = K3 column FFT / divide / inverse,
+ * 3 = K4 row inverse FFTs.  blfls_profile_end waits for the recorded events and writes, per
+ * stage, the summed device time in milliseconds (ms[4]) and the number of launches
+ * (launches[4]); either pointer may be NULL.  Events beyond max_events are not recorded and
+ * make blfls_profile_end return BLFLS_EINVAL. */
+int blfls_profile_begin(blfls_handle *h, int max_events);
+int blfls_profile_end(blfls_handle *h, double *ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLFLS_H */

@@ -1,0 +1,486 @@
+// C ABI of the BLF-LS smoother (declarations and contracts in include/blfls.h).
+//
+// A handle owns the FFT plans (per transform length), the per-channel scratch (the two gradient
+// residual planes of step 1 and the half spectrum of step 2) and, for the host-buffer entry
+// point, device copies of the image.  Calls validate on the host, grow scratch when needed
+// (within the byte budget), then enqueue for every iteration and channel:
+//   K1 (bilateral residuals) -> K2 (row FFTs) -> K3 (column FFTs, divide, inverse) -> K4 (row
+//   inverse FFTs, u = f + correction).
+#include "blfls.h"
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+using namespace blfls;
+
+struct blfls_handle {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+    int col_block = 4;
+    std::map<int, FftPlanHost> plans;
+    // scratch (device)
+    float* ex = nullptr;
+    float* ey = nullptr;
+    size_t e_cap = 0;  // floats per plane
+    float2* spec = nullptr;
+    size_t spec_cap = 0;  // complex values
+    float* gscratch = nullptr;
+    size_t g_cap = 0;
+    float* io = nullptr;  // device copies for blfls_smooth_host: img then out
+    size_t io_cap = 0;
+    // kernel timing (blfls_profile_begin / _end)
+    bool prof_on = false;
+    bool prof_overflow = false;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_next = 0;
+    std::vector<std::pair<int, std::pair<int, int>>> prof_spans;  // stage, (start, end) event
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(BLFLS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Make the handle's device current for the duration of a call and restore the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool budget_allows(blfls_handle* h, size_t extra)
+{
+    return h->budget == 0 || h->used + extra <= h->budget;
+}
+
+template <typename T>
+int grow(blfls_handle* h, T*& ptr, size_t& cap, size_t need, const char* what)
+{
+    if (need <= cap) return BLFLS_OK;
+    const size_t old_bytes = cap * sizeof(T), new_bytes = need * sizeof(T);
+    if (!budget_allows(h, new_bytes - old_bytes))
+        return fail(BLFLS_ENOMEM, std::string("scratch for ") + what + " exceeds the memory budget");
+    if (ptr) {
+        cudaFree(ptr);  // waits for work still using it
+        h->used -= old_bytes;
+        ptr = nullptr;
+        cap = 0;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, new_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BLFLS_ENOMEM, std::string("cudaMalloc for ") + what + ": " + cudaGetErrorString(e));
+    }
+    ptr = static_cast<T*>(p);
+    cap = need;
+    h->used += new_bytes;
+    return BLFLS_OK;
+}
+
+int get_plan(blfls_handle* h, int N, const FftPlanDev** out)
+{
+    auto it = h->plans.find(N);
+    if (it == h->plans.end()) {
+        FftPlanHost p;
+        const cudaError_t e = build_fft_plan(N, p);
+        if (e != cudaSuccess) return cuda_fail(e, "FFT plan");
+        if (!budget_allows(h, p.bytes)) {
+            free_fft_plan(p);
+            return fail(BLFLS_ENOMEM, "FFT plan exceeds the memory budget");
+        }
+        h->used += p.bytes;
+        it = h->plans.emplace(N, p).first;
+    }
+    *out = &it->second.dev;
+    return BLFLS_OK;
+}
+
+int check_image_args(const void* a, const void* b, int H, int W, int C)
+{
+    if (!a || !b) return fail(BLFLS_EINVAL, "image pointer is NULL");
+    if (H < 1 || W < 1 || H > BLFLS_MAX_DIM || W > BLFLS_MAX_DIM)
+        return fail(BLFLS_EINVAL, "H and W must lie in [1, BLFLS_MAX_DIM]");
+    if (C < 1 || C > BLFLS_MAX_CHANNELS) return fail(BLFLS_EINVAL, "C must lie in [1, BLFLS_MAX_CHANNELS]");
+    return BLFLS_OK;
+}
+
+int check_blf_args(int H, int W, float sigma_s, float sigma_r, int radius, int prec)
+{
+    if (radius < 0 || 2LL * radius + 1 > (long long)std::min(H, W))
+        return fail(BLFLS_EINVAL, "radius must satisfy 0 <= radius and 2*radius+1 <= min(H, W)");
+    if (!(sigma_s > 0.f)) return fail(BLFLS_EINVAL, "sigma_s must be > 0");
+    if (!(sigma_r > 0.f)) return fail(BLFLS_EINVAL, "sigma_r must be > 0");
+    if (prec < BLFLS_FP32 || prec > BLFLS_BF16W) return fail(BLFLS_EINVAL, "unknown precision");
+    if (prec != BLFLS_FP32) return fail(BLFLS_EINVAL, "this build has only the FP32 bilateral path");
+    return BLFLS_OK;
+}
+
+int check_lambda(float lambda)
+{
+    if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(BLFLS_EINVAL, "lambda must be finite and >= 0");
+    return BLFLS_OK;
+}
+
+}  // namespace
+
+// The residual planes ex/ey share one capacity; keep them in lock-step.
+static int ensure_residual_planes(blfls_handle* h, size_t plane)
+{
+    if (plane <= h->e_cap && h->ex && h->ey) return BLFLS_OK;
+    const size_t old_bytes = 2 * h->e_cap * sizeof(float), new_bytes = 2 * plane * sizeof(float);
+    if (!budget_allows(h, new_bytes - std::min(old_bytes, new_bytes)))
+        return fail(BLFLS_ENOMEM, "scratch for gradient residuals exceeds the memory budget");
+    if (h->ex) cudaFree(h->ex);
+    h->used -= old_bytes;
+    h->ex = h->ey = nullptr;
+    h->e_cap = 0;
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, new_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BLFLS_ENOMEM, std::string("cudaMalloc for gradient residuals: ") + cudaGetErrorString(e));
+    }
+    h->ex = static_cast<float*>(p);
+    h->ey = h->ex + plane;
+    h->e_cap = plane;
+    h->used += new_bytes;
+    return BLFLS_OK;
+}
+
+static int prepare(blfls_handle* h, int H, int W, int radius, bool need_blf, bool need_solve,
+                   const FftPlanDev** rp, const FftPlanDev** cp)
+{
+    int rc;
+    const size_t plane = (size_t)H * W;
+    if ((rc = ensure_residual_planes(h, plane)) != BLFLS_OK) return rc;
+    if (need_blf && radius > blf_tiled_max_radius())
+        if ((rc = grow(h, h->gscratch, h->g_cap, 2 * plane, "gradients")) != BLFLS_OK) return rc;
+    if (need_solve) {
+        if ((rc = grow(h, h->spec, h->spec_cap, (size_t)H * (W / 2 + 1), "spectrum")) != BLFLS_OK) return rc;
+        if ((rc = get_plan(h, W, rp)) != BLFLS_OK) return rc;
+        if ((rc = get_plan(h, H, cp)) != BLFLS_OK) return rc;
+    }
+    return BLFLS_OK;
+}
+
+// Take the next pre-created profiling event and record it on s; -1 when profiling is off or the
+// pool is exhausted.
+static int prof_mark(blfls_handle* h, cudaStream_t s)
+{
+    if (!h->prof_on) return -1;
+    if (h->prof_next >= h->prof_pool.size()) {
+        h->prof_overflow = true;
+        return -1;
+    }
+    const int i = int(h->prof_next++);
+    cudaEventRecord(h->prof_pool[i], s);
+    return i;
+}
+
+static void prof_span(blfls_handle* h, int stage, int a, int b)
+{
+    if (a >= 0 && b >= 0) h->prof_spans.push_back({stage, {a, b}});
+}
+
+// K1 on `C` channels with optional timing.
+static cudaError_t blf_launch(blfls_handle* h, const float* img, float* ex, float* ey, int C,
+                              const BlfParams& bp, cudaStream_t s)
+{
+    const int a = prof_mark(h, s);
+    const cudaError_t e = launch_blf_residual(img, ex, ey, C, bp, h->gscratch, s);
+    prof_span(h, 0, a, prof_mark(h, s));
+    return e;
+}
+
+// K2-K4 on one channel with optional timing.
+static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex, const float* ey,
+                                float* out, const FftPlanDev& rp, const FftPlanDev& cp,
+                                const SolveParams& sp, cudaStream_t s)
+{
+    const int a = prof_mark(h, s);
+    cudaEvent_t marks[2];
+    int mi[2] = {-1, -1};
+    const bool timed = a >= 0 && h->prof_next + 3 <= h->prof_pool.size();
+    if (timed) {
+        mi[0] = int(h->prof_next++);
+        mi[1] = int(h->prof_next++);
+        marks[0] = h->prof_pool[mi[0]];
+        marks[1] = h->prof_pool[mi[1]];
+    }
+    const cudaError_t e = launch_solve_residual(f, ex, ey, out, h->spec, rp, cp, rp.lap, cp.lap, sp,
+                                                s, h->num_sms, timed ? marks : nullptr);
+    const int b = timed ? prof_mark(h, s) : -1;
+    if (timed) {
+        prof_span(h, 1, a, mi[0]);
+        prof_span(h, 2, mi[0], mi[1]);
+        prof_span(h, 3, mi[1], b);
+    } else if (h->prof_on) {
+        h->prof_overflow = true;
+    }
+    return e;
+}
+
+static int run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                      float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
+                      cudaStream_t s)
+{
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out != img) {
+            const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                                  cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "copy for iters = 0");
+        }
+        return BLFLS_OK;
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    int rc = prepare(h, H, W, radius, true, true, &rp, &cp);
+    if (rc != BLFLS_OK) return rc;
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec};
+    const SolveParams sp{H, W, lambda, h->col_block};
+    for (int it = 0; it < iters; ++it) {
+        const float* src = (it == 0) ? img : out;
+        for (int c = 0; c < C; ++c) {
+            cudaError_t e = blf_launch(h, src + c * plane, h->ex, h->ey, 1, bp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
+            e = solve_launch(h, src + c * plane, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+        }
+    }
+    return BLFLS_OK;
+}
+
+extern "C" {
+
+int blfls_create(blfls_handle** out, int device, size_t mem_budget_bytes,
+                 const char* tune_table_path)
+{
+    if (!out) return fail(BLFLS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(BLFLS_EINVAL, "no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    blfls_handle* h = new blfls_handle();
+    h->device = device;
+    h->budget = mem_budget_bytes;
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    init_blf_kernel_attributes();
+    init_solve_kernel_attributes();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "kernel attributes");
+    }
+    (void)tune_table_path;
+    *out = h;
+    return BLFLS_OK;
+}
+
+void blfls_destroy(blfls_handle* h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
+    for (auto& kv : h->plans) free_fft_plan(kv.second);
+    if (h->ex) cudaFree(h->ex);
+    if (h->spec) cudaFree(h->spec);
+    if (h->gscratch) cudaFree(h->gscratch);
+    if (h->io) cudaFree(h->io);
+    delete h;
+}
+
+const char* blfls_last_error(blfls_handle* h)
+{
+    (void)h;
+    return g_last_error.c_str();
+}
+
+int blfls_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                 float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
+                 void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    return run_smooth(h, img, out, H, W, C, lambda, sigma_s, sigma_r, radius, iters, prec,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int blfls_smooth_host(blfls_handle* h, const float* img_host, float* out_host, int H, int W,
+                      int C, float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                      int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img_host, out_host, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    const size_t n = (size_t)H * W * C;
+    if ((rc = grow(h, h->io, h->io_cap, 2 * n, "host-buffer staging")) != BLFLS_OK) return rc;
+    float* dimg = h->io;
+    float* dout = h->io + n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(dimg, img_host, n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    rc = run_smooth(h, dimg, dout, H, W, C, lambda, sigma_s, sigma_r, radius, iters, prec, s);
+    if (rc != BLFLS_OK) return rc;
+    e = cudaMemcpyAsync(out_host, dout, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return BLFLS_OK;
+}
+
+int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, int H, int W,
+                       int C, float sigma_s, float sigma_r, int radius, int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, ex, H, W, C)) != BLFLS_OK) return rc;
+    if (!ey) return fail(BLFLS_EINVAL, "ey is NULL");
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    if (radius > blf_tiled_max_radius())
+        if ((rc = grow(h, h->gscratch, h->g_cap, 2 * (size_t)H * W, "gradients")) != BLFLS_OK) return rc;
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec};
+    const cudaError_t e = blf_launch(h, img, ex, ey, C, bp, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
+    return BLFLS_OK;
+}
+
+int blfls_solve_residual(blfls_handle* h, const float* img, const float* ex, const float* ey,
+                         float* out, int H, int W, int C, float lambda, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if (!ex || !ey) return fail(BLFLS_EINVAL, "residual pointer is NULL");
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = grow(h, h->spec, h->spec_cap, (size_t)H * (W / 2 + 1), "spectrum")) != BLFLS_OK) return rc;
+    if ((rc = get_plan(h, W, &rp)) != BLFLS_OK) return rc;
+    if ((rc = get_plan(h, H, &cp)) != BLFLS_OK) return rc;
+    const size_t plane = (size_t)H * W;
+    const SolveParams sp{H, W, lambda, h->col_block};
+    for (int c = 0; c < C; ++c) {
+        const cudaError_t e = solve_launch(h, img + c * plane, ex + c * plane, ey + c * plane,
+                                           out + c * plane, *rp, *cp, sp,
+                                           static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+    }
+    return BLFLS_OK;
+}
+
+int blfls_smooth_batch(blfls_handle* h, const blfls_job* jobs, int n, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    if (n < 0 || (n > 0 && !jobs)) return fail(BLFLS_EINVAL, "bad job list");
+    for (int i = 0; i < n; ++i) {
+        const blfls_job& j = jobs[i];
+        int rc;
+        if ((rc = check_image_args(j.img, j.out, j.H, j.W, j.C)) != BLFLS_OK) return rc;
+        if ((rc = check_blf_args(j.H, j.W, j.sigma_s, j.sigma_r, j.radius, j.prec)) != BLFLS_OK) return rc;
+        if ((rc = check_lambda(j.lambda)) != BLFLS_OK) return rc;
+        if (j.iters < 0 || j.iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters out of range");
+    }
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    for (int i = 0; i < n; ++i) {
+        const blfls_job& j = jobs[i];
+        const int rc = run_smooth(h, j.img, j.out, j.H, j.W, j.C, j.lambda, j.sigma_s, j.sigma_r,
+                                  j.radius, j.iters, j.prec, static_cast<cudaStream_t>(stream));
+        if (rc != BLFLS_OK) return rc;
+    }
+    return BLFLS_OK;
+}
+
+int blfls_profile_begin(blfls_handle* h, int max_events)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    if (max_events < 0) return fail(BLFLS_EINVAL, "max_events must be >= 0");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    while (h->prof_pool.size() < (size_t)max_events) {
+        cudaEvent_t ev;
+        const cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        h->prof_pool.push_back(ev);
+    }
+    h->prof_on = true;
+    h->prof_overflow = false;
+    h->prof_next = 0;
+    h->prof_spans.clear();
+    return BLFLS_OK;
+}
+
+int blfls_profile_end(blfls_handle* h, double* ms, int* launches)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    h->prof_on = false;
+    double tot[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (const auto& sp : h->prof_spans) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(h->prof_pool[sp.second.second]);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&t, h->prof_pool[sp.second.first], h->prof_pool[sp.second.second]);
+        if (e != cudaSuccess) return cuda_fail(e, "profiling events");
+        tot[sp.first] += t;
+        cnt[sp.first] += 1;
+    }
+    for (int i = 0; i < 4; ++i) {
+        if (ms) ms[i] = tot[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    if (h->prof_overflow) return fail(BLFLS_EINVAL, "more launches than profiling events");
+    return BLFLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+// CTA-wide in-place FFTs on shared memory, used by the Fourier solve of Eq. 8.
+//
+// A "column set" is `ncols` interleaved transforms: element n of column c sits at
+// x[n * ncols + c] (ncols a power of two; 1 for a single row).  All threads of the CTA take part;
+// every routine starts by assuming its input is visible to all threads (the caller synchronised)
+// and ends with a __syncthreads().
+//
+// Direct transforms (length L = product of the plan's radices):
+//   forward: decimation in frequency, natural input -> output in digit-reversed order
+//            (frequency k at position perm[k]);
+//   inverse: the conjugate stages in reverse order, digit-reversed input -> natural output,
+//            unnormalised (a forward-then-inverse pair multiplies by L).
+// Bluestein transforms (length N not 7-smooth) convert the length-N DFT into a cyclic
+// convolution of length L = 2^k >= 2N-1 carried out by the direct transforms; input and output
+// are in natural order, positions [N, L) are scratch.
+#pragma once
+
+#include "internal.h"
+
+namespace blfls {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// -i * a (forward rotation) or +i * a (inverse rotation)
+template <bool INV>
+__device__ __forceinline__ float2 rot_i(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi k / R) and sin(2 pi k / R) for the odd radices (mathematical constants).
+__device__ __forceinline__ constexpr float root_cos(int R, int k)
+{
+    return R == 3 ? -0.5f
+         : R == 5 ? (k == 1 ? 0.309016994374947424f : -0.809016994374947424f)
+         : /* 7 */  (k == 1 ? 0.623489801858733531f
+                   : k == 2 ? -0.222520933956314404f : -0.900968867902419126f);
+}
+__device__ __forceinline__ constexpr float root_sin(int R, int k)
+{
+    return R == 3 ? 0.866025403784438647f
+         : R == 5 ? (k == 1 ? 0.951056516295153572f : 0.587785252292473129f)
+         : /* 7 */  (k == 1 ? 0.781831482468029809f
+                   : k == 2 ? 0.974927912181823607f : 0.433883739117558120f);
+}
+
+// In-register R-point DFT, y_q = sum_t x_t w^(t q), w = exp(-+2 pi i / R).
+template <int R, bool INV>
+__device__ __forceinline__ void small_dft(float2 (&v)[R])
+{
+    if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const float2 c = cadd(v[1], v[3]), d = rot_i<INV>(csub(v[1], v[3]));
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    } else {
+        // odd R: pair t with R-t; y_q = x0 + sum_t [(x_t + x_{R-t}) cos -/+ i (x_t - x_{R-t}) sin]
+        constexpr int h = (R - 1) / 2;
+        float2 s[h + 1], d[h + 1];
+#pragma unroll
+        for (int t = 1; t <= h; ++t) {
+            s[t] = cadd(v[t], v[R - t]);
+            d[t] = csub(v[t], v[R - t]);
+        }
+        const float2 x0 = v[0];
+        float2 y0 = x0;
+#pragma unroll
+        for (int t = 1; t <= h; ++t) y0 = cadd(y0, s[t]);
+#pragma unroll
+        for (int q = 1; q <= h; ++q) {
+            float2 re = x0, im = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 1; t <= h; ++t) {
+                const int k = (t * q) % R;
+                const float c = root_cos(R, k <= h ? k : R - k);
+                const float sn = (k <= h ? 1.f : -1.f) * root_sin(R, k <= h ? k : R - k);
+                re.x = fmaf(s[t].x, c, re.x);
+                re.y = fmaf(s[t].y, c, re.y);
+                im.x = fmaf(d[t].x, sn, im.x);
+                im.y = fmaf(d[t].y, sn, im.y);
+            }
+            const float2 r = rot_i<INV>(im);  // -i*im forward, +i*im inverse
+            v[q] = cadd(re, r);
+            v[R - q] = csub(re, r);
+        }
+        v[0] = y0;
+    }
+}
+
+// One decimation-in-frequency stage over blocks of length Lblk = R*m:
+//   inputs x[base + t m], base = blk*Lblk + j;  R-point DFT;  output q times w_Lblk^(j q).
+template <int R>
+__device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc, int Lw, int Lblk,
+                                          int tw_step, const float2* __restrict__ tw)
+{
+    const int ncols = 1 << lgc;
+    const int m = Lblk / R;
+    const int total = (Lw / R) << lgc;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int col = b & (ncols - 1);
+        const int bi = b >> lgc;
+        const int blk = bi / m;
+        const int j = bi - blk * m;
+        const int base = blk * Lblk + j;
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = x[((base + t * m) << lgc) + col];
+        small_dft<R, false>(v);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 w = q ? tw[j * q * tw_step] : make_float2(1.f, 0.f);
+            x[((base + q * m) << lgc) + col] = q ? cmul(v[q], w) : v[q];
+        }
+    }
+}
+
+// The inverse of dif_stage (up to the factor R): inputs times conj(w_Lblk^(j q)), inverse DFT.
+template <int R>
+__device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc, int Lw, int Lblk,
+                                              int tw_step, const float2* __restrict__ tw)
+{
+    const int ncols = 1 << lgc;
+    const int m = Lblk / R;
+    const int total = (Lw / R) << lgc;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int col = b & (ncols - 1);
+        const int bi = b >> lgc;
+        const int blk = bi / m;
+        const int j = bi - blk * m;
+        const int base = blk * Lblk + j;
+        float2 v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 a = x[((base + q * m) << lgc) + col];
+            v[q] = q ? cmulc(a, tw[j * q * tw_step]) : a;
+        }
+        small_dft<R, true>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) x[((base + t * m) << lgc) + col] = v[t];
+    }
+}
+
+__device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlanDev& p,
+                                               const float2* tw)
+{
+    const int Lw = p.L;
+    int Lblk = Lw;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        const int tw_step = Lw / Lblk;
+        switch (R) {
+            case 4: dif_stage<4>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 2: dif_stage<2>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 3: dif_stage<3>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 5: dif_stage<5>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            default: dif_stage<7>(x, lgc, Lw, Lblk, tw_step, tw); break;
+        }
+        __syncthreads();
+        Lblk /= R;
+    }
+}
+
+__device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlanDev& p,
+                                               const float2* tw)
+{
+    const int Lw = p.L;
+    int Lblk = 1;
+    for (int s = p.nst - 1; s >= 0; --s) {
+        const int R = p.radix[s];
+        Lblk *= R;
+        const int tw_step = Lw / Lblk;
+        switch (R) {
+            case 4: dit_inv_stage<4>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 2: dit_inv_stage<2>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 3: dit_inv_stage<3>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 5: dit_inv_stage<5>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            default: dit_inv_stage<7>(x, lgc, Lw, Lblk, tw_step, tw); break;
+        }
+        __syncthreads();
+    }
+}
+
+// Bluestein: X_k = c_k sum_n (x_n c_n) conj(c_{k-n}),  c_n = exp(-i pi n^2 / N).
+// The inverse transform conjugates input and output.
+template <bool INV>
+__device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& p,
+                                          const float2* tw)
+{
+    const int ncols = 1 << lgc;
+    const int N = p.N, Lw = p.L;
+    for (int i = threadIdx.x; i < (Lw << lgc); i += blockDim.x) {
+        const int n = i >> lgc;
+        float2 v = make_float2(0.f, 0.f);
+        if (n < N) {
+            float2 a = x[i];
+            if (INV) a = cconj(a);
+            v = cmul(a, __ldg(p.chirp + n));
+        }
+        x[i] = v;
+    }
+    __syncthreads();
+    direct_forward(x, lgc, p, tw);
+    for (int i = threadIdx.x; i < (Lw << lgc); i += blockDim.x)
+        x[i] = cmul(x[i], __ldg(p.bhat + (i >> lgc)));
+    __syncthreads();
+    direct_inverse(x, lgc, p, tw);
+    for (int i = threadIdx.x; i < (N << lgc); i += blockDim.x) {
+        const float2 v = cmul(x[i], __ldg(p.chirp + (i >> lgc)));
+        x[i] = INV ? cconj(v) : v;
+    }
+    __syncthreads();
+    (void)ncols;
+}
+
+// Forward DFT of every column: natural input; frequency k ends at position perm[k].
+__device__ __forceinline__ void fft_forward(float2* x, int lgc, const FftPlanDev& p,
+                                            const float2* tw)
+{
+    if (p.bluestein) bluestein<false>(x, lgc, p, tw);
+    else direct_forward(x, lgc, p, tw);
+}
+
+// Unnormalised inverse DFT: frequency k read from position perm[k]; natural output.
+__device__ __forceinline__ void fft_inverse(float2* x, int lgc, const FftPlanDev& p,
+                                            const float2* tw)
+{
+    if (p.bluestein) bluestein<true>(x, lgc, p, tw);
+    else direct_inverse(x, lgc, p, tw);
+}
+
+}  // namespace blfls

@@ -1,0 +1,178 @@
+// FFT plans for the Fourier solve of Eq. 8: factorisation, twiddles, digit-reversal tables and
+// Bluestein chirps.  Every table is computed in FP64 on the host and stored as FP32.
+#include "internal.h"
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+namespace blfls {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Digit-reversed position of every frequency for an in-place decimation-in-frequency FFT with
+// stages radices[0..m-1]: k = q0 + R0 q1 + R0 R1 q2 + ...  sits at  sum_s q_s * (N / (R0..Rs)).
+std::vector<int> dif_positions(int N, const std::vector<int>& radices)
+{
+    std::vector<int> pos(N);
+    for (int k = 0; k < N; ++k) {
+        int rem = k, span = N, p = 0;
+        for (int R : radices) {
+            const int q = rem % R;
+            rem /= R;
+            span /= R;
+            p += q * span;
+        }
+        pos[k] = p;
+    }
+    return pos;
+}
+
+// Plain FP64 radix-2 FFT (length a power of two), forward sign exp(-2 pi i nk/N).
+void host_fft_pow2(std::vector<std::complex<double>>& a)
+{
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t i = 0; i < n; i += len) {
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double ang = -2.0 * kPi * double(k) / double(len);
+                const std::complex<double> w(std::cos(ang), std::sin(ang));
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+bool factor_direct(int N, std::vector<int>& radices)
+{
+    radices.clear();
+    if (N < 1) return false;
+    int n = N;
+    while (n % 4 == 0) { radices.push_back(4); n /= 4; }
+    if (n % 2 == 0) { radices.push_back(2); n /= 2; }
+    while (n % 3 == 0) { radices.push_back(3); n /= 3; }
+    while (n % 5 == 0) { radices.push_back(5); n /= 5; }
+    while (n % 7 == 0) { radices.push_back(7); n /= 7; }
+    return n == 1 && int(radices.size()) <= kMaxStages;
+}
+
+cudaError_t build_fft_plan(int N, FftPlanHost& out)
+{
+    out = FftPlanHost{};
+    FftPlanDev& d = out.dev;
+    d.N = N;
+    std::vector<int> radices;
+    const bool direct = factor_direct(N, radices);
+    int L = N;
+    if (!direct) {
+        L = 1;
+        while (L < 2 * N - 1) L <<= 1;
+        factor_direct(L, radices);
+    }
+    if (L > kMaxFftLen) return cudaErrorInvalidValue;
+    d.L = L;
+    d.bluestein = direct ? 0 : 1;
+    d.nst = int(radices.size());
+    for (int s = 0; s < d.nst; ++s) d.radix[s] = radices[s];
+
+    // Host tables.
+    std::vector<float2> tw(L);
+    for (int m = 0; m < L; ++m) {
+        const double ang = -2.0 * kPi * double(m) / double(L);
+        tw[m] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+    }
+    const std::vector<int> posL = dif_positions(L, radices);
+    std::vector<int> iperm(L);
+    for (int k = 0; k < L; ++k) iperm[posL[k]] = k;
+    std::vector<int> perm(N);
+    std::vector<float2> chirp, bhat;
+    if (direct) {
+        perm = posL;
+    } else {
+        for (int k = 0; k < N; ++k) perm[k] = k;
+        for (int p = 0; p < L; ++p) iperm[p] = p;
+        // c_n = exp(-i pi n^2 / N), with n^2 reduced mod 2N in integers to keep the angle exact.
+        std::vector<std::complex<double>> c(N);
+        chirp.resize(N);
+        for (int n = 0; n < N; ++n) {
+            const long long q = (long long)n * n % (2LL * N);
+            const double ang = -kPi * double(q) / double(N);
+            c[n] = std::complex<double>(std::cos(ang), std::sin(ang));
+            chirp[n] = make_float2(float(c[n].real()), float(c[n].imag()));
+        }
+        std::vector<std::complex<double>> b(L, 0.0);
+        for (int n = 0; n < N; ++n) {
+            b[n] = std::conj(c[n]);
+            if (n > 0) b[L - n] = std::conj(c[n]);
+        }
+        host_fft_pow2(b);
+        bhat.resize(L);
+        for (int k = 0; k < L; ++k) {
+            const std::complex<double> v = b[k] / double(L);
+            bhat[posL[k]] = make_float2(float(v.real()), float(v.imag()));
+        }
+    }
+
+    std::vector<float> lap(N);
+    for (int k = 0; k < N; ++k) {
+        const double sn = std::sin(kPi * double(k) / double(N));
+        lap[k] = float(4.0 * sn * sn);
+    }
+
+    // One device allocation: tw | chirp | bhat | perm | iperm | lap.
+    const size_t o_tw = 0;
+    const size_t o_chirp = align256(o_tw + sizeof(float2) * L);
+    const size_t o_bhat = align256(o_chirp + sizeof(float2) * chirp.size());
+    const size_t o_perm = align256(o_bhat + sizeof(float2) * bhat.size());
+    const size_t o_iperm = align256(o_perm + sizeof(int) * N);
+    const size_t o_lap = align256(o_iperm + sizeof(int) * L);
+    const size_t bytes = align256(o_lap + sizeof(float) * N);
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * L);
+    if (!chirp.empty()) std::memcpy(host.data() + o_chirp, chirp.data(), sizeof(float2) * N);
+    if (!bhat.empty()) std::memcpy(host.data() + o_bhat, bhat.data(), sizeof(float2) * L);
+    std::memcpy(host.data() + o_perm, perm.data(), sizeof(int) * N);
+    std::memcpy(host.data() + o_iperm, iperm.data(), sizeof(int) * L);
+    std::memcpy(host.data() + o_lap, lap.data(), sizeof(float) * N);
+
+    void* dmem = nullptr;
+    cudaError_t e = cudaMalloc(&dmem, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(dmem, host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dmem);
+        return e;
+    }
+    unsigned char* base = static_cast<unsigned char*>(dmem);
+    d.tw = reinterpret_cast<const float2*>(base + o_tw);
+    d.chirp = chirp.empty() ? nullptr : reinterpret_cast<const float2*>(base + o_chirp);
+    d.bhat = bhat.empty() ? nullptr : reinterpret_cast<const float2*>(base + o_bhat);
+    d.perm = reinterpret_cast<const int*>(base + o_perm);
+    d.iperm = reinterpret_cast<const int*>(base + o_iperm);
+    d.lap = reinterpret_cast<const float*>(base + o_lap);
+    out.dmem = dmem;
+    out.bytes = bytes;
+    return cudaSuccess;
+}
+
+void free_fft_plan(FftPlanHost& p)
+{
+    if (p.dmem) cudaFree(p.dmem);
+    p = FftPlanHost{};
+}
+
+}  // namespace blfls

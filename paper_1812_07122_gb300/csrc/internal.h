@@ -1,0 +1,90 @@
+// Internal declarations shared by the BLF-LS CUDA sources (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace blfls {
+
+// ---------------------------------------------------------------------------------------------
+// FFT plans.  A transform of length N is either a direct in-place mixed-radix FFT (N factors
+// into 2, 3, 4, 5, 7) or Bluestein's chirp-z algorithm over a direct power-of-two FFT of length
+// L >= 2N - 1.  The direct forward transform is decimation in frequency: natural-order input,
+// output in mixed-radix digit-reversed order, so frequency k sits at position perm[k].  The
+// inverse runs the conjugate stages in reverse order and takes that order back to natural.
+// Bluestein transforms use natural order on both sides (perm is the identity for its users).
+// All tables are computed in FP64 on the host and stored as FP32 (complex as float2).
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxStages = 16;
+constexpr int kMaxFftLen = 16384;  // longest direct transform (Bluestein work length)
+
+struct FftPlanDev {
+    int N;          // transform length
+    int L;          // work length in shared memory (N, or the Bluestein length)
+    int nst;        // number of direct stages
+    int bluestein;  // 0 / 1
+    int radix[kMaxStages];
+    const float2* tw;      // L entries: exp(-2 pi i m / L)
+    const int* perm;       // N entries: work position of frequency k (identity for Bluestein)
+    const int* iperm;      // L entries: frequency held at work position p (direct only)
+    const float2* chirp;   // N entries (Bluestein): exp(-i pi n^2 / N)
+    const float2* bhat;    // L entries (Bluestein): DFT_L of the conjugate chirp / L, in the
+                           // direct transform's position order
+    const float* lap;      // N entries: 4 sin^2(pi k / N), the periodic Laplacian's eigenvalues
+};
+
+struct FftPlanHost {
+    FftPlanDev dev{};
+    void* dmem = nullptr;  // one device allocation holding every table
+    size_t bytes = 0;
+};
+
+// Factor N for the direct path; returns false when N has a prime factor above 7.
+bool factor_direct(int N, std::vector<int>& radices);
+// Build the host tables of a plan and upload them (cudaMalloc'd, owned by the caller).
+cudaError_t build_fft_plan(int N, FftPlanHost& out);
+void free_fft_plan(FftPlanHost& p);
+
+// ---------------------------------------------------------------------------------------------
+// Bilateral step (K1): for each channel, ex = BLF(D_x f) - D_x f and ey likewise.
+// ---------------------------------------------------------------------------------------------
+struct BlfParams {
+    int H, W;
+    int radius;
+    float sigma_s, sigma_r;
+    int prec;  // blfls_precision
+};
+
+// Launch K1 over channels [0, C) of img (planes of H*W floats).  `gscratch` must hold
+// 2*H*W floats when the radius is above the tiled kernels' limit (else may be null).
+void init_blf_kernel_attributes();
+void init_solve_kernel_attributes();
+
+cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C,
+                                const BlfParams& p, float* gscratch, cudaStream_t s);
+int blf_tiled_max_radius();
+
+// ---------------------------------------------------------------------------------------------
+// Fourier solve (K2 rows forward, K3 columns forward / divide / inverse, K4 rows inverse).
+// spec holds H rows of W/2+1 complex values.
+// ---------------------------------------------------------------------------------------------
+struct SolveParams {
+    int H, W;
+    float lambda;
+    int col_block;   // columns per CTA in K3 (power of two, 1..16)
+};
+
+// `marks` (nullable) receives two events recorded after K2 and after K3.
+cudaError_t launch_solve_residual(const float* f, const float* ex, const float* ey, float* out,
+                                  float2* spec, const FftPlanDev& rowp, const FftPlanDev& colp,
+                                  const float* sx, const float* sy, const SolveParams& p,
+                                  cudaStream_t s, int num_sms, const cudaEvent_t* marks = nullptr);
+
+// Smallest/largest shared memory the solve kernels need for these plans (bytes).
+size_t solve_smem_rows(const FftPlanDev& rowp);
+size_t solve_smem_cols(const FftPlanDev& colp, int col_block);
+
+}  // namespace blfls
