@@ -136,6 +136,37 @@ int blfls_smooth_batch(blfls_handle *h, const blfls_job *jobs, int n, void *stre
 int blfls_profile_begin(blfls_handle *h, int max_events);
 int blfls_profile_end(blfls_handle *h, double *ms, int *launches);
 
+/* Step 2 without any device allocation (the paper has no counterpart; this is a deployment
+ * variant of blfls_solve_residual).
+ *
+ * For callers that cannot call cudaMalloc/cudaFree: a plug-in whose host application owns all
+ * device memory through its own arena, or a real-time video path that cannot afford an
+ * allocation's possible device-wide synchronisation.  It computes exactly what
+ * blfls_solve_residual computes, on the calling thread's current device and without a handle.
+ * The caller passes inputs and outputs as usual (device pointers, [C][H][W] FP32); the scratch
+ * (the half spectrum and the FFT tables) lives in one static device array of
+ * BLFLS_NOALLOC_SPECTRUM_BYTES + BLFLS_NOALLOC_TABLE_BYTES bytes that every GPU loading this
+ * library keeps until the process exits.
+ *
+ * Limits: 1 <= H, W <= BLFLS_NOALLOC_MAX_DIM and H * (W/2 + 1) * 8 <= BLFLS_NOALLOC_SPECTRUM_BYTES
+ * (1024 x 1024 fits); larger sizes return BLFLS_EINVAL with a message and launch nothing.
+ * No cudaMalloc, cudaFree or allocating library call is made.
+ *
+ * The first call on a device sets up that device (looks up the static array's device address,
+ * the SM count and the kernels' shared-memory limits); make that first call before any stream
+ * capture begins on the device.  A call whose size differs from the previous call's copies new
+ * FFT tables into the array from host memory, ordered on `stream`.
+ * Every call shares the one array, which keeps the previous call's contents; each call
+ * overwrites all of the scratch it reads.  Calls that overlap on the GPU (for example on two
+ * streams of one device) race on the array: issue them on one stream, one after another.  The
+ * host-side bookkeeping is protected by a lock, so calling from several threads is safe as long
+ * as the GPU work itself does not overlap. */
+#define BLFLS_NOALLOC_SPECTRUM_BYTES 4456448u /* 4.25 MiB: H * (W/2+1) <= 557056 */
+#define BLFLS_NOALLOC_TABLE_BYTES 1048576u    /* 1 MiB of FFT tables */
+#define BLFLS_NOALLOC_MAX_DIM 4096
+int blfls_solve_residual_noalloc(const float *img, const float *ex, const float *ey, float *out,
+                                 int H, int W, int C, float lambda, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

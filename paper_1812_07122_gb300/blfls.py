@@ -66,6 +66,8 @@ _SIGNATURES = {
                                       _c_float, _vp]),
     "blfls_smooth_batch": (_c_int, [_vp, ctypes.POINTER(blfls_job), _c_int, _vp]),
     "blfls_profile_begin": (_c_int, [_vp, _c_int]),
+    "blfls_solve_residual_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int,
+                                              _c_float, _vp]),
     "blfls_profile_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
 }
 
@@ -163,6 +165,12 @@ def blfls_blf_residual(h, img, ex, ey, H, W, C, sigma_s, sigma_r, radius, prec=B
 def blfls_solve_residual(h, img, ex, ey, out, H, W, C, lam, stream=None) -> None:
     _check(load().blfls_solve_residual(h, _ptr(img), _ptr(ex), _ptr(ey), _ptr(out), int(H),
                                        int(W), int(C), float(lam), _stream(stream)), h)
+
+
+def blfls_solve_residual_noalloc(img, ex, ey, out, H, W, C, lam, stream=None) -> None:
+    """The solve step without device allocation; scratch is the library's static array."""
+    _check(load().blfls_solve_residual_noalloc(_ptr(img), _ptr(ex), _ptr(ey), _ptr(out), int(H),
+                                               int(W), int(C), float(lam), _stream(stream)))
 
 
 def make_job(img, out, H, W, C, lam, sigma_s, sigma_r, radius, iters=1, prec=BLFLS_FP32):

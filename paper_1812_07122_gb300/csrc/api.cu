@@ -149,6 +149,8 @@ int check_lambda(float lambda)
 
 }  // namespace
 
+void blfls::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 // The residual planes ex/ey share one capacity; keep them in lock-step.
 static int ensure_residual_planes(blfls_handle* h, size_t plane)
 {

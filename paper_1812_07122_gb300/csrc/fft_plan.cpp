@@ -175,4 +175,101 @@ void free_fft_plan(FftPlanHost& p)
     p = FftPlanHost{};
 }
 
+// The same tables as build_fft_plan, laid out in one host blob instead of a device allocation.
+// `rel` receives the plan with every table pointer holding its byte offset inside the blob;
+// bind_fft_tables turns those offsets into addresses once the blob sits at `base`.
+bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& rel)
+{
+    rel = FftPlanDev{};
+    rel.N = N;
+    std::vector<int> radices;
+    const bool direct = factor_direct(N, radices);
+    int L = N;
+    if (!direct) {
+        L = 1;
+        while (L < 2 * N - 1) L <<= 1;
+        factor_direct(L, radices);
+    }
+    if (L > kMaxFftLen) return false;
+    rel.L = L;
+    rel.bluestein = direct ? 0 : 1;
+    rel.nst = int(radices.size());
+    for (int s = 0; s < rel.nst; ++s) rel.radix[s] = radices[s];
+
+    std::vector<float2> tw(L);
+    for (int m = 0; m < L; ++m) {
+        const double ang = -2.0 * kPi * double(m) / double(L);
+        tw[m] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+    }
+    const std::vector<int> posL = dif_positions(L, radices);
+    std::vector<int> iperm(L);
+    for (int k = 0; k < L; ++k) iperm[posL[k]] = k;
+    std::vector<int> perm(N);
+    std::vector<float2> chirp, bhat;
+    if (direct) {
+        perm = posL;
+    } else {
+        for (int k = 0; k < N; ++k) perm[k] = k;
+        for (int p = 0; p < L; ++p) iperm[p] = p;
+        std::vector<std::complex<double>> c(N);
+        chirp.resize(N);
+        for (int n = 0; n < N; ++n) {
+            const long long q = (long long)n * n % (2LL * N);
+            const double ang = -kPi * double(q) / double(N);
+            c[n] = std::complex<double>(std::cos(ang), std::sin(ang));
+            chirp[n] = make_float2(float(c[n].real()), float(c[n].imag()));
+        }
+        std::vector<std::complex<double>> b(L, 0.0);
+        for (int n = 0; n < N; ++n) {
+            b[n] = std::conj(c[n]);
+            if (n > 0) b[L - n] = std::conj(c[n]);
+        }
+        host_fft_pow2(b);
+        bhat.resize(L);
+        for (int k = 0; k < L; ++k) {
+            const std::complex<double> v = b[k] / double(L);
+            bhat[posL[k]] = make_float2(float(v.real()), float(v.imag()));
+        }
+    }
+    std::vector<float> lap(N);
+    for (int k = 0; k < N; ++k) {
+        const double sn = std::sin(kPi * double(k) / double(N));
+        lap[k] = float(4.0 * sn * sn);
+    }
+    const size_t o_tw = 0;
+    const size_t o_chirp = align256(o_tw + sizeof(float2) * L);
+    const size_t o_bhat = align256(o_chirp + sizeof(float2) * chirp.size());
+    const size_t o_perm = align256(o_bhat + sizeof(float2) * bhat.size());
+    const size_t o_iperm = align256(o_perm + sizeof(int) * N);
+    const size_t o_lap = align256(o_iperm + sizeof(int) * L);
+    const size_t bytes = align256(o_lap + sizeof(float) * N);
+    blob.assign(bytes, 0);
+    std::memcpy(blob.data() + o_tw, tw.data(), sizeof(float2) * L);
+    if (!chirp.empty()) std::memcpy(blob.data() + o_chirp, chirp.data(), sizeof(float2) * N);
+    if (!bhat.empty()) std::memcpy(blob.data() + o_bhat, bhat.data(), sizeof(float2) * L);
+    std::memcpy(blob.data() + o_perm, perm.data(), sizeof(int) * N);
+    std::memcpy(blob.data() + o_iperm, iperm.data(), sizeof(int) * L);
+    std::memcpy(blob.data() + o_lap, lap.data(), sizeof(float) * N);
+    rel.tw = reinterpret_cast<const float2*>(o_tw);
+    rel.chirp = chirp.empty() ? nullptr : reinterpret_cast<const float2*>(o_chirp);
+    rel.bhat = bhat.empty() ? nullptr : reinterpret_cast<const float2*>(o_bhat);
+    rel.perm = reinterpret_cast<const int*>(o_perm);
+    rel.iperm = reinterpret_cast<const int*>(o_iperm);
+    rel.lap = reinterpret_cast<const float*>(o_lap);
+    return true;
+}
+
+FftPlanDev bind_fft_tables(const FftPlanDev& rel, const void* base)
+{
+    const unsigned char* b = static_cast<const unsigned char*>(base);
+    FftPlanDev d = rel;
+    d.tw = reinterpret_cast<const float2*>(b + reinterpret_cast<size_t>(rel.tw));
+    d.chirp = rel.chirp ? reinterpret_cast<const float2*>(b + reinterpret_cast<size_t>(rel.chirp)) : nullptr;
+    d.bhat = rel.bhat ? reinterpret_cast<const float2*>(b + reinterpret_cast<size_t>(rel.bhat)) : nullptr;
+    d.perm = reinterpret_cast<const int*>(b + reinterpret_cast<size_t>(rel.perm));
+    d.iperm = reinterpret_cast<const int*>(b + reinterpret_cast<size_t>(rel.iperm));
+    d.lap = reinterpret_cast<const float*>(b + reinterpret_cast<size_t>(rel.lap));
+    return d;
+}
+
 }  // namespace blfls

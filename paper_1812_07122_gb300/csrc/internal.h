@@ -47,6 +47,12 @@ bool factor_direct(int N, std::vector<int>& radices);
 // Build the host tables of a plan and upload them (cudaMalloc'd, owned by the caller).
 cudaError_t build_fft_plan(int N, FftPlanHost& out);
 void free_fft_plan(FftPlanHost& p);
+// Host-only variant for callers that place the tables themselves: fills `blob` and returns the
+// plan with table offsets in place of pointers; bind_fft_tables rebases them onto `base`.
+bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& rel);
+FftPlanDev bind_fft_tables(const FftPlanDev& rel, const void* base);
+// Record the message returned by blfls_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------------------------------------
 // Bilateral step (K1): for each channel, ex = BLF(D_x f) - D_x f and ey likewise.
