@@ -39,7 +39,6 @@ METRIC = "BLF-LS megapixels/s at 4K RGB, batched/FP16 vs plain FP32; p99 latency
 H, W, C = 2160, 3840, 3
 PARAMS = dict(lam=30.0, sigma_s=5.0, sigma_r=0.08, radius=10, iters=3)
 WORKLOAD = "3840x2160 RGB FP32, radius 10, sigma_s 5, sigma_r 0.08, lambda 30, 3 passes"
-MUFU_EX2_PER_CLK_PER_SM = 16    # FP32 ex2 results per clock per SM (sm_100-class SFU)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -52,6 +51,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -169,11 +172,115 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(h, dev, stream, flush, steps):
+    """64 uneven jobs (sizes log-uniform, C in {1,3}, per-job lambda, sigma_r, radius): one
+    blfls_smooth_batch call (graph-replayed) vs. a loop of blfls_smooth calls, both timed with
+    events after an L2 flush."""
+    import torch
+    from paper_1812_07122_gb300 import blfls, synth
+    jobs = synth.batch_jobs(64, seed=4)
+    xs, ys, cj = [], [], []
+    for j in jobs:
+        x = torch.from_numpy(synth.job_image(j)).to(dev)
+        y = torch.empty_like(x)
+        xs.append(x)
+        ys.append(y)
+        cj.append(blfls.make_job(x, y, j.H, j.W, j.C, j.lam, j.sigma_s, j.sigma_r, j.radius,
+                                 j.iters))
+    mp = sum(j.H * j.W for j in jobs) / 1e6
+
+    def loop():
+        for j, x, y in zip(jobs, xs, ys):
+            blfls.blfls_smooth(h, x, y, j.H, j.W, j.C, j.lam, j.sigma_s, j.sigma_r, j.radius,
+                               j.iters, 0, stream)
+
+    def batch():
+        blfls.blfls_smooth_batch(h, cj, stream)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for i in range(n):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / n
+
+    n = max(3, steps // 6)
+    t_batch = timed(batch, n)
+    t_loop = timed(loop, n)
+    return {"workload": "64 jobs, H log-uniform 256-1536, W 256-2048, C in {1,3}, lambda~U[5,50], "
+                        "sigma_r~U[0.05,0.2], radius in {3,5,8,10}, sigma_s=r/2, 1 pass, FP32",
+            "megapixels_per_call": round(mp, 2), "ms_batched": round(t_batch, 3),
+            "ms_single_loop": round(t_loop, 3), "batched_mp_per_s": round(mp / t_batch * 1e3, 1),
+            "single_loop_mp_per_s": round(mp / t_loop * 1e3, 1),
+            "speedup": round(t_loop / t_batch, 3), "launch": "graph replay of one persistent "
+                        "launch per phase (K1 per radius group, K2, K3, K4)"}
+
+
+def bench_serving(dev, n_req, rate):
+    """Poisson arrivals of jobs with H, W log-uniform 128-4096, C in {1,3}, parameters as in
+    the batched workload, served with an 80 GB budget from pinned host buffers; then the same
+    server saturated (all requests queued at once) for its capacity."""
+    import torch
+    from paper_1812_07122_gb300 import blfls, synth
+    reqs = synth.serving_requests(n_req, seed=5, rate_hz=rate)
+    pool_img = synth.sinusoid_disc_image(4096, 4096, 3, 400, 0.03, seed=55)
+    src = torch.from_numpy(pool_img.reshape(-1)).pin_memory()
+    dst = torch.empty_like(src).pin_memory()
+    n_pool = src.numel()
+    rng = __import__("numpy").random.default_rng(6)
+    base_in, base_out = src.data_ptr(), dst.data_ptr()
+
+    def request(j):
+        need = j.C * j.H * j.W
+        off = int(rng.integers(0, (n_pool - need) // 64 + 1)) * 64
+        return blfls.make_request(base_in + 4 * off, base_out + 4 * off, j.H, j.W, j.C, j.lam,
+                                  j.sigma_s, j.sigma_r, j.radius, j.iters)
+
+    def run(jobs, paced):
+        srv = blfls.blfls_server_create(dev.index or 0, 80 << 30, slots=4, max_batch=16)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            for j in jobs:
+                if paced:
+                    delay = j.arrival_s - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets.append(blfls.blfls_server_submit(srv, request(j)))
+            for t in tickets:
+                blfls.blfls_server_wait(srv, t, 600000)
+            return blfls.blfls_server_get_stats(srv)
+        finally:
+            blfls.blfls_server_destroy(srv)
+
+    warm = run(reqs[:64], paced=False)          # plans and graphs for common shapes
+    st = run(reqs, paced=True)
+    sat = run(reqs[: min(len(reqs), 2000)], paced=False)
+    keep = ["completed", "failed", "p50_ms", "p99_ms", "mean_ms", "max_ms", "megapixels",
+            "busy_s", "mp_per_s", "max_batch_seen", "device_bytes_peak"]
+    return {"workload": f"{n_req} requests, Poisson {rate:g} req/s, H,W log-uniform 128-4096, "
+                        "C in {1,3}, lambda~U[5,50], sigma_r~U[0.05,0.2], radius in {3,5,8,10}, "
+                        "pinned host buffers, budget 80 GB, 4 slots, batches <= 16",
+            "poisson": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()
+                        if k in keep},
+            "saturated_2000": {k: (round(v, 3) if isinstance(v, float) else v)
+                               for k, v in sat.items() if k in keep},
+            "warmup_requests": warm["completed"]}
+
+
 def k1_traffic_per_launch():
     """DRAM bytes per K1 launch from the committed ncu summary, if it was taken on the current
     kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "k1_blf_4k_traffic.json")
-    src = os.path.join(ROOT, "paper_1812_07122_gb300", "csrc", "blf_kernels.cu")
+    src = os.path.join(ROOT, "paper_1812_07122_gb300", "csrc", "blf_tile.cuh")
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -225,6 +332,9 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
+    rates = blfls.blfls_pipe_rates(local)                # results / clk / SM, measured here
+    ex2_per_clk = rates["ex2_f32"]
+    ex2_units = float(2 ** round(math.log2(ex2_per_clk))) if ex2_per_clk > 0 else 32.0
 
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -260,13 +370,15 @@ def main():
     k1_ms = prof_ms[0] / max(prof_n[0], 1)
     achieved = taps_per_launch / (k1_ms / 1e3) / 1e9                    # Gtap/s
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = MUFU_EX2_PER_CLK_PER_SM * n_sm * sm_mhz * 1e6 / 1e9
+    peak = ex2_units * n_sm * sm_mhz * 1e6 / 1e9
     total_prof = sum(prof_ms)
     roofline = {"bound": "alu", "kernel": "k1_blf_tiled<10,range> (bilateral residuals)",
                 "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Gtap/s",
                 "frac": round(achieved / peak, 4), "traffic": k1_traffic_per_launch(),
-                "peak_basis": f"MUFU ex2: {MUFU_EX2_PER_CLK_PER_SM}/clk/SM x {n_sm} SMs x "
-                              f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed loop)",
+                "peak_basis": f"MUFU ex2.f32: {ex2_units:.0f}/clk/SM (probe measured "
+                              f"{ex2_per_clk:.2f}) x {n_sm} SMs x {sm_mhz:.0f} MHz (median SM "
+                              f"clock sampled in the timed loop); one ex2 per tap",
+                "pipe_rates_per_clk_per_sm": {k: round(v, 2) for k, v in rates.items()},
                 "k1_ms_per_launch": round(k1_ms, 4),
                 "stage_share": {k: round(v / total_prof, 4) for k, v in
                                 zip(["K1", "K2", "K3", "K4"], prof_ms)} if total_prof else None}
@@ -318,6 +430,13 @@ def main():
             except blfls.BlflsError as e:
                 forms[name] = f"unavailable: {e}"
 
+    batched = None
+    if not args.no_batch:
+        batched = bench_batched(h, dev, stream, flush, K)
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = bench_serving(dev, args.serve_requests, args.serve_rate)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -338,7 +457,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * K, "clocks": clocks, "forms": forms}
+                "gpu_launches": launches_per_step * K, "clocks": clocks, "forms": forms,
+                "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

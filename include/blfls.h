@@ -62,12 +62,17 @@ typedef enum {
     BLFLS_EBUSY = -5     /* the serving queue is full */
 } blfls_status;
 
-/* Arithmetic of the bilateral window (step 1).  The Fourier solve is FP32 in every mode. */
+/* Arithmetic of the bilateral window (step 1).  The Fourier solve is FP32 in every mode.
+ * FP16W/BF16W accept radius <= BLFLS_MAX_HALF_RADIUS (BLFLS_EINVAL above). */
 typedef enum {
-    BLFLS_FP32 = 0,  /* weights, products and sums in FP32 */
-    BLFLS_FP16W = 1, /* weights exp(.) and products w*g in FP16 (half2); sums in FP32 */
-    BLFLS_BF16W = 2  /* weights and products in BF16 (bfloat162); sums in FP32 */
+    BLFLS_FP32 = 0,  /* exponent, weights, products and sums in FP32 */
+    BLFLS_FP16W = 1, /* gradient values, exponent, weights exp(.) and products w*g in FP16
+                        (half2); each window column's sums in FP16, accumulated across columns
+                        in FP32 */
+    BLFLS_BF16W = 2  /* exponent in FP32; weights exp(.) computed and rounded in BF16
+                        (bfloat162); products and sums in FP32 */
 } blfls_precision;
+#define BLFLS_MAX_HALF_RADIUS 16
 
 /* Create a handle on CUDA device `device`.  mem_budget_bytes caps the scratch memory the
  * handle may allocate (0 = no cap).  tune_table_path names a tile-shape table written by the
@@ -125,6 +130,60 @@ typedef struct {
  * of blfls_smooth on each job alone (same kernels, same arithmetic). */
 int blfls_smooth_batch(blfls_handle *h, const blfls_job *jobs, int n, void *stream);
 
+/* ---- Served form (no counterpart in the paper): continuous batching on one GPU ------------
+ *
+ * A server owns one device arena (a fixed share of mem_budget_bytes, allocated at creation) from
+ * which every request's input and output buffers are carved, `slots` concurrent streams each
+ * with its own resident handle (FFT plans and scratch, capped by the slot's share of the budget),
+ * and a scheduler thread.  Requests carry HOST buffers.  Whenever a slot is free the scheduler
+ * takes queued requests in arrival order, first fit -- a request joins the batch if its buffers
+ * fit in the arena and the batch's scratch fits the slot -- up to max_batch of them, copies them
+ * in, smooths them with one blfls_smooth_batch call and copies the results out, all on the
+ * slot's stream, so batches on different slots overlap on the device.  A request's result is the
+ * same as blfls_smooth on it alone.  Budget split: 60% arena, 35% slot scratch, 5% plans and
+ * tables.  Latency is measured from submit to the result being in host memory. */
+typedef struct blfls_server blfls_server;
+
+typedef struct {
+    const float *img_host; /* host [C][H][W]: read until the request completes */
+    float *out_host;       /* host [C][H][W]: written when the request completes */
+    int H, W, C;
+    float lambda, sigma_s, sigma_r;
+    int radius, iters;
+    int prec; /* blfls_precision */
+} blfls_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, rejected;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result in host memory */
+    double megapixels;                      /* sum of H*W over completed requests */
+    double busy_s;                          /* first submit -> last completion */
+    double mp_per_s;                        /* megapixels / busy_s */
+    size_t device_bytes_peak;               /* arena peak + handles' scratch and plans */
+    size_t device_bytes_budget;
+    int max_batch_seen;
+} blfls_server_stats;
+
+/* Create a server on `device` with 1..16 slots and batches of at most max_batch (1..1024)
+ * requests; mem_budget_bytes >= 64 MiB.  Errors: BLFLS_EINVAL, BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_server_create(blfls_server **out, int device, size_t mem_budget_bytes, int slots,
+                        int max_batch, const char *tune_table_path);
+/* Cancel queued requests, finish running ones, free everything.  NULL-safe. */
+void blfls_server_destroy(blfls_server *s);
+/* Queue a request; returns at once with a ticket.  Arguments are validated here (BLFLS_EINVAL);
+ * a request that could never fit the budget is rejected with BLFLS_ENOMEM.  The caller keeps
+ * img_host and out_host alive until the request has finished or been cancelled. */
+int blfls_server_submit(blfls_server *s, const blfls_request *r, uint64_t *ticket);
+/* *state: 0 queued or running, 1 done, 2 cancelled, < 0 the error code it failed with. */
+int blfls_server_poll(blfls_server *s, uint64_t ticket, int *state);
+/* Wait up to timeout_ms for the request: BLFLS_OK when done, BLFLS_ETIMEOUT, or its error. */
+int blfls_server_wait(blfls_server *s, uint64_t ticket, int timeout_ms);
+/* Cancel a request that has not been admitted yet (BLFLS_EBUSY once it is running or done). */
+int blfls_server_cancel(blfls_server *s, uint64_t ticket);
+/* Forget a finished or cancelled request's record (BLFLS_EBUSY while queued or running). */
+int blfls_server_release(blfls_server *s, uint64_t ticket);
+int blfls_server_get_stats(blfls_server *s, blfls_server_stats *out);
+
 /* Kernel timing (no counterpart in the paper; measurement support for the benchmark).
  * blfls_profile_begin pre-creates `max_events` CUDA events and starts recording an event pair
  * around every kernel launch the handle makes, on the launch's own stream.  Stages:
@@ -135,6 +194,24 @@ int blfls_smooth_batch(blfls_handle *h, const blfls_job *jobs, int n, void *stre
  * make blfls_profile_end return BLFLS_EINVAL. */
 int blfls_profile_begin(blfls_handle *h, int max_events);
 int blfls_profile_end(blfls_handle *h, double *ms, int *launches);
+
+/* Autotuner (no counterpart in the paper; launch shapes only, results never change).  Times the
+ * candidate K1 tile heights for (radius, prec) and the candidate K3 column blocks for columns of
+ * length H on a synthetic H x W x C image generated on the device, keeps the fastest in the
+ * handle (used by every later call on it), and, if table_path is not NULL, writes the handle's
+ * whole table there as JSON (readable by blfls_create).  Synchronous; allocates temporary device
+ * buffers of 3*H*W*C floats plus one spectrum (outside the handle's budget).
+ * Errors: BLFLS_EINVAL (bad sizes, or an unwritable table_path), BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_autotune(blfls_handle *h, int H, int W, int C, int radius, int prec,
+                   const char *table_path);
+
+/* Measured throughput of the arithmetic pipes the bilateral kernels use (no counterpart in the
+ * paper; measurement support for the roofline).  On `device`, writes up to n of: rates[0] FP32
+ * FFMA results, [1] packed fma.f32x2 FP32 results, [2] MUFU ex2.f32 results, [3] ex2.f16x2 FP16
+ * results, [4] ex2.bf16x2 BF16 results -- each per clock per SM, from clock64 cycle counts of
+ * one fully occupied block per SM.  Synchronous; allocates (and frees) a few bytes of device
+ * memory.  Returns BLFLS_EINVAL for a bad device or rates == NULL. */
+int blfls_pipe_rates(int device, double *rates, int n);
 
 /* Step 2 without any device allocation (the paper has no counterpart; this is a deployment
  * variant of blfls_solve_residual).

@@ -47,6 +47,25 @@ class blfls_job(ctypes.Structure):
                 ("prec", ctypes.c_int)]
 
 
+class blfls_request(ctypes.Structure):
+    _fields_ = [("img_host", ctypes.c_void_p), ("out_host", ctypes.c_void_p),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
+                ("lambda_", ctypes.c_float), ("sigma_s", ctypes.c_float),
+                ("sigma_r", ctypes.c_float), ("radius", ctypes.c_int), ("iters", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class blfls_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("megapixels", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("mp_per_s", ctypes.c_double),
+                ("device_bytes_peak", ctypes.c_size_t), ("device_bytes_budget", ctypes.c_size_t),
+                ("max_batch_seen", ctypes.c_int)]
+
+
 _LIB = None
 
 _c_int, _c_float, _vp, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
@@ -66,6 +85,18 @@ _SIGNATURES = {
                                       _c_float, _vp]),
     "blfls_smooth_batch": (_c_int, [_vp, ctypes.POINTER(blfls_job), _c_int, _vp]),
     "blfls_profile_begin": (_c_int, [_vp, _c_int]),
+    "blfls_server_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _sz, _c_int, _c_int,
+                                     ctypes.c_char_p]),
+    "blfls_server_destroy": (None, [_vp]),
+    "blfls_server_submit": (_c_int, [_vp, ctypes.POINTER(blfls_request),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "blfls_server_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_c_int)]),
+    "blfls_server_wait": (_c_int, [_vp, ctypes.c_uint64, _c_int]),
+    "blfls_server_cancel": (_c_int, [_vp, ctypes.c_uint64]),
+    "blfls_server_release": (_c_int, [_vp, ctypes.c_uint64]),
+    "blfls_server_get_stats": (_c_int, [_vp, ctypes.POINTER(blfls_server_stats)]),
+    "blfls_autotune": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.c_char_p]),
+    "blfls_pipe_rates": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double), _c_int]),
     "blfls_solve_residual_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int,
                                               _c_float, _vp]),
     "blfls_profile_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
@@ -183,6 +214,11 @@ def blfls_smooth_batch(h, jobs, stream=None) -> None:
     _check(load().blfls_smooth_batch(h, arr, len(jobs), _stream(stream)), h)
 
 
+def blfls_autotune(h, H, W, C, radius, prec=BLFLS_FP32, table_path: str | None = None) -> None:
+    path = table_path.encode() if table_path else None
+    _check(load().blfls_autotune(h, int(H), int(W), int(C), int(radius), _prec(prec), path), h)
+
+
 def blfls_profile_begin(h, max_events: int) -> None:
     _check(load().blfls_profile_begin(h, int(max_events)), h)
 
@@ -193,6 +229,66 @@ def blfls_profile_end(h):
     n = (ctypes.c_int * 4)()
     _check(load().blfls_profile_end(h, ms, n), h)
     return list(ms), list(n)
+
+
+PIPE_RATE_NAMES = ["ffma_f32", "ffma2_f32", "ex2_f32", "ex2_f16x2", "ex2_bf16x2"]
+
+
+def blfls_pipe_rates(device: int = 0) -> dict:
+    """Results per clock per SM of each arithmetic pipe, measured on the device."""
+    r = (ctypes.c_double * 5)()
+    _check(load().blfls_pipe_rates(int(device), r, 5))
+    return dict(zip(PIPE_RATE_NAMES, list(r)))
+
+
+def blfls_server_create(device=0, mem_budget_bytes=80 << 30, slots=4, max_batch=16,
+                        tune_table_path=None):
+    srv = _vp()
+    path = tune_table_path.encode() if tune_table_path else None
+    _check(load().blfls_server_create(ctypes.byref(srv), int(device), int(mem_budget_bytes),
+                                      int(slots), int(max_batch), path))
+    return srv
+
+
+def blfls_server_destroy(srv) -> None:
+    if srv is not None:
+        load().blfls_server_destroy(srv)
+
+
+def make_request(img_host, out_host, H, W, C, lam, sigma_s, sigma_r, radius, iters=1,
+                 prec=BLFLS_FP32):
+    return blfls_request(_ptr(img_host), _ptr(out_host), int(H), int(W), int(C), float(lam),
+                         float(sigma_s), float(sigma_r), int(radius), int(iters), _prec(prec))
+
+
+def blfls_server_submit(srv, req) -> int:
+    t = ctypes.c_uint64()
+    _check(load().blfls_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def blfls_server_poll(srv, ticket) -> int:
+    st = ctypes.c_int()
+    _check(load().blfls_server_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(st)))
+    return st.value
+
+
+def blfls_server_wait(srv, ticket, timeout_ms=60000) -> None:
+    _check(load().blfls_server_wait(srv, ctypes.c_uint64(ticket), int(timeout_ms)))
+
+
+def blfls_server_cancel(srv, ticket) -> None:
+    _check(load().blfls_server_cancel(srv, ctypes.c_uint64(ticket)))
+
+
+def blfls_server_release(srv, ticket) -> None:
+    _check(load().blfls_server_release(srv, ctypes.c_uint64(ticket)))
+
+
+def blfls_server_get_stats(srv) -> dict:
+    st = blfls_server_stats()
+    _check(load().blfls_server_get_stats(srv, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
 
 
 class Smoother:

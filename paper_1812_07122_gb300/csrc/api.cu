@@ -7,7 +7,7 @@
 //   K1 (bilateral residuals) -> K2 (row FFTs) -> K3 (column FFTs, divide, inverse) -> K4 (row
 //   inverse FFTs, u = f + correction).
 #include "blfls.h"
-#include "internal.h"
+#include "handle.h"
 
 #include <cmath>
 #include <cstdio>
@@ -17,79 +17,38 @@
 
 using namespace blfls;
 
-struct blfls_handle {
-    int device = 0;
-    int num_sms = 0;
-    size_t budget = 0;  // 0 = unlimited
-    size_t used = 0;
-    int col_block = 4;
-    std::map<int, FftPlanHost> plans;
-    // scratch (device)
-    float* ex = nullptr;
-    float* ey = nullptr;
-    size_t e_cap = 0;  // floats per plane
-    float2* spec = nullptr;
-    size_t spec_cap = 0;  // complex values
-    float* gscratch = nullptr;
-    size_t g_cap = 0;
-    float* io = nullptr;  // device copies for blfls_smooth_host: img then out
-    size_t io_cap = 0;
-    // kernel timing (blfls_profile_begin / _end)
-    bool prof_on = false;
-    bool prof_overflow = false;
-    std::vector<cudaEvent_t> prof_pool;
-    size_t prof_next = 0;
-    std::vector<std::pair<int, std::pair<int, int>>> prof_spans;  // stage, (start, end) event
-};
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-int fail(int code, const std::string& msg)
+int blfls::fail(int code, const std::string& msg)
 {
     g_last_error = msg;
     return code;
 }
 
-int cuda_fail(cudaError_t e, const char* where)
+int blfls::cuda_fail(cudaError_t e, const char* where)
 {
     return fail(BLFLS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Make the handle's device current for the duration of a call and restore the caller's.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-bool budget_allows(blfls_handle* h, size_t extra)
+bool blfls::budget_allows(blfls_handle* h, size_t extra)
 {
     return h->budget == 0 || h->used + extra <= h->budget;
 }
 
-template <typename T>
-int grow(blfls_handle* h, T*& ptr, size_t& cap, size_t need, const char* what)
+int blfls::grow_bytes(blfls_handle* h, void** ptr, size_t* cap_bytes, size_t need, const char* what)
 {
-    if (need <= cap) return BLFLS_OK;
-    const size_t old_bytes = cap * sizeof(T), new_bytes = need * sizeof(T);
+    if (need <= *cap_bytes) return BLFLS_OK;
+    const size_t old_bytes = *cap_bytes, new_bytes = need;
     if (!budget_allows(h, new_bytes - old_bytes))
         return fail(BLFLS_ENOMEM, std::string("scratch for ") + what + " exceeds the memory budget");
-    if (ptr) {
-        cudaFree(ptr);  // waits for work still using it
+    if (*ptr) {
+        cudaFree(*ptr);  // waits for work still using it
         h->used -= old_bytes;
-        ptr = nullptr;
-        cap = 0;
+        *ptr = nullptr;
+        *cap_bytes = 0;
     }
     void* p = nullptr;
     const cudaError_t e = cudaMalloc(&p, new_bytes);
@@ -97,13 +56,27 @@ int grow(blfls_handle* h, T*& ptr, size_t& cap, size_t need, const char* what)
         cudaGetLastError();
         return fail(BLFLS_ENOMEM, std::string("cudaMalloc for ") + what + ": " + cudaGetErrorString(e));
     }
-    ptr = static_cast<T*>(p);
-    cap = need;
+    *ptr = p;
+    *cap_bytes = need;
     h->used += new_bytes;
+    h->generation++;
     return BLFLS_OK;
 }
 
-int get_plan(blfls_handle* h, int N, const FftPlanDev** out)
+namespace {
+template <typename T>
+int grow(blfls_handle* h, T*& ptr, size_t& cap, size_t need, const char* what)
+{
+    void* p = ptr;
+    size_t bytes = cap * sizeof(T);
+    const int rc = blfls::grow_bytes(h, &p, &bytes, need * sizeof(T), what);
+    ptr = static_cast<T*>(p);
+    cap = bytes / sizeof(T);
+    return rc;
+}
+}  // namespace
+
+int blfls::get_plan(blfls_handle* h, int N, const FftPlanDev** out)
 {
     auto it = h->plans.find(N);
     if (it == h->plans.end()) {
@@ -121,7 +94,7 @@ int get_plan(blfls_handle* h, int N, const FftPlanDev** out)
     return BLFLS_OK;
 }
 
-int check_image_args(const void* a, const void* b, int H, int W, int C)
+int blfls::check_image_args(const void* a, const void* b, int H, int W, int C)
 {
     if (!a || !b) return fail(BLFLS_EINVAL, "image pointer is NULL");
     if (H < 1 || W < 1 || H > BLFLS_MAX_DIM || W > BLFLS_MAX_DIM)
@@ -130,24 +103,23 @@ int check_image_args(const void* a, const void* b, int H, int W, int C)
     return BLFLS_OK;
 }
 
-int check_blf_args(int H, int W, float sigma_s, float sigma_r, int radius, int prec)
+int blfls::check_blf_args(int H, int W, float sigma_s, float sigma_r, int radius, int prec)
 {
     if (radius < 0 || 2LL * radius + 1 > (long long)std::min(H, W))
         return fail(BLFLS_EINVAL, "radius must satisfy 0 <= radius and 2*radius+1 <= min(H, W)");
     if (!(sigma_s > 0.f)) return fail(BLFLS_EINVAL, "sigma_s must be > 0");
     if (!(sigma_r > 0.f)) return fail(BLFLS_EINVAL, "sigma_r must be > 0");
     if (prec < BLFLS_FP32 || prec > BLFLS_BF16W) return fail(BLFLS_EINVAL, "unknown precision");
-    if (prec != BLFLS_FP32) return fail(BLFLS_EINVAL, "this build has only the FP32 bilateral path");
+    if (prec != BLFLS_FP32 && radius > BLFLS_MAX_HALF_RADIUS)
+        return fail(BLFLS_EINVAL, "the FP16W/BF16W forms support radius <= BLFLS_MAX_HALF_RADIUS");
     return BLFLS_OK;
 }
 
-int check_lambda(float lambda)
+int blfls::check_lambda(float lambda)
 {
     if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(BLFLS_EINVAL, "lambda must be finite and >= 0");
     return BLFLS_OK;
 }
-
-}  // namespace
 
 void blfls::set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -172,6 +144,7 @@ static int ensure_residual_planes(blfls_handle* h, size_t plane)
     h->ey = h->ex + plane;
     h->e_cap = plane;
     h->used += new_bytes;
+    h->generation++;
     return BLFLS_OK;
 }
 
@@ -248,7 +221,7 @@ static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex
     return e;
 }
 
-static int run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
                       float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
                       cudaStream_t s)
 {
@@ -264,8 +237,8 @@ static int run_smooth(blfls_handle* h, const float* img, float* out, int H, int 
     const FftPlanDev *rp = nullptr, *cp = nullptr;
     int rc = prepare(h, H, W, radius, true, true, &rp, &cp);
     if (rc != BLFLS_OK) return rc;
-    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec};
-    const SolveParams sp{H, W, lambda, h->col_block};
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
         for (int c = 0; c < C; ++c) {
@@ -306,7 +279,7 @@ int blfls_create(blfls_handle** out, int device, size_t mem_budget_bytes,
         delete h;
         return cuda_fail(e, "kernel attributes");
     }
-    (void)tune_table_path;
+    load_tune_table(h, tune_table_path);
     *out = h;
     return BLFLS_OK;
 }
@@ -317,6 +290,7 @@ void blfls_destroy(blfls_handle* h)
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
     for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
+    destroy_batch_state(h->batch);
     for (auto& kv : h->plans) free_fft_plan(kv.second);
     if (h->ex) cudaFree(h->ex);
     if (h->spec) cudaFree(h->spec);
@@ -387,7 +361,7 @@ int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, 
     if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
     if (radius > blf_tiled_max_radius())
         if ((rc = grow(h, h->gscratch, h->g_cap, 2 * (size_t)H * W, "gradients")) != BLFLS_OK) return rc;
-    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec};
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
     const cudaError_t e = blf_launch(h, img, ex, ey, C, bp, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
     return BLFLS_OK;
@@ -408,7 +382,7 @@ int blfls_solve_residual(blfls_handle* h, const float* img, const float* ex, con
     if ((rc = get_plan(h, W, &rp)) != BLFLS_OK) return rc;
     if ((rc = get_plan(h, H, &cp)) != BLFLS_OK) return rc;
     const size_t plane = (size_t)H * W;
-    const SolveParams sp{H, W, lambda, h->col_block};
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
     for (int c = 0; c < C; ++c) {
         const cudaError_t e = solve_launch(h, img + c * plane, ex + c * plane, ey + c * plane,
                                            out + c * plane, *rp, *cp, sp,
@@ -432,13 +406,7 @@ int blfls_smooth_batch(blfls_handle* h, const blfls_job* jobs, int n, void* stre
     }
     DeviceGuard g(h->device);
     if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
-    for (int i = 0; i < n; ++i) {
-        const blfls_job& j = jobs[i];
-        const int rc = run_smooth(h, j.img, j.out, j.H, j.W, j.C, j.lambda, j.sigma_s, j.sigma_r,
-                                  j.radius, j.iters, j.prec, static_cast<cudaStream_t>(stream));
-        if (rc != BLFLS_OK) return rc;
-    }
-    return BLFLS_OK;
+    return run_batch(h, jobs, n, static_cast<cudaStream_t>(stream));
 }
 
 int blfls_profile_begin(blfls_handle* h, int max_events)

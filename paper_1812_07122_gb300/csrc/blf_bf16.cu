@@ -1,0 +1,35 @@
+// K1 kernel instantiations of the BF16 form, radii 0..16 (single-image and batched
+// drivers).  Split by precision so the three translation units compile in parallel.
+#include "blf_tile.cuh"
+
+namespace blfls {
+namespace {
+
+template <int R>
+TiledFn pick_tiled_bf16(int r, bool range)
+{
+    if constexpr (R > kMaxTemplR) {
+        return nullptr;
+    } else {
+        if (r != R) return pick_tiled_bf16<R + 1>(r, range);
+        return range ? k1_blf<R, true, 2> : k1_blf<R, false, 2>;
+    }
+}
+
+template <int R>
+BatchFn pick_batch_bf16(int r, bool range)
+{
+    if constexpr (R > kMaxTemplR) {
+        return nullptr;
+    } else {
+        if (r != R) return pick_batch_bf16<R + 1>(r, range);
+        return range ? k1_blf_batch<R, true, 2> : k1_blf_batch<R, false, 2>;
+    }
+}
+
+}  // namespace
+
+TiledFn pick_tiled_bf16_entry(int r, bool range) { return pick_tiled_bf16<0>(r, range); }
+BatchFn pick_batch_bf16_entry(int r, bool range) { return pick_batch_bf16<0>(r, range); }
+
+}  // namespace blfls

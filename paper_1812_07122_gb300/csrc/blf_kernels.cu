@@ -1,180 +1,59 @@
-// Step 1 of BLF-LS (Section III-A): the bilateral filter of Eq. 1 on the periodic forward-
-// difference gradients (Section II-B), emitted as residuals e_* = f_BLF(g_*) - g_*.
-//
-// K1 (tiled): one CTA per 32x32 output tile of one channel.  It loads the image tile with an
-// (r+1)-pixel periodic halo into shared memory, forms both gradient fields on the tile + r halo
-// (pre-scaled by kappa = sqrt(log2(e) / (2 sigma_r^2)) so that a range weight is a single
-// exp2(a - d^2)), and then each thread filters a vertical strip of 8 pixels of both fields.
-// For every window column dx the thread streams the 8 + 2r field values of that column once
-// from shared memory and reuses each against every strip pixel it reaches, so the inner loop
-// is register-resident: per tap one subtract, one FMA for the exponent (the spatial log-weight
-// of (dx, dy) folded in), one MUFU ex2 and two accumulations.
-// Radii up to kMaxTemplR are compiled with the window fully unrolled per column; larger radii up
-// to kMaxTiledR use the same tiling with a runtime window loop; above that a plain per-pixel
-// kernel reads precomputed gradients from global memory.
-#include "internal.h"
-
-#include <cmath>
+// Step 1 of BLF-LS (Section III-A): dispatch of the bilateral kernels, plus the kernels for radii
+// above the unrolled range (a scalar tiled kernel with a runtime window, and a per-pixel kernel
+// over precomputed gradients).  The unrolled kernels live in blf_tile.cuh and are instantiated
+// per precision in blf_f32.cu, blf_f16.cu and blf_bf16.cu.
+#include "blf_tile.cuh"
 
 namespace blfls {
 
+TiledFn pick_tiled_f32_entry(int r, bool range);
+TiledFn pick_tiled_f16_entry(int r, bool range);
+TiledFn pick_tiled_bf16_entry(int r, bool range);
+BatchFn pick_batch_f32_entry(int r, bool range);
+BatchFn pick_batch_f16_entry(int r, bool range);
+BatchFn pick_batch_bf16_entry(int r, bool range);
+
+TiledFn pick_tiled_prec(int prec, int r, bool range)
+{
+    if (prec == 1) return pick_tiled_f16_entry(r, range);
+    if (prec == 2) return pick_tiled_bf16_entry(r, range);
+    return pick_tiled_f32_entry(r, range);
+}
+
+BatchFn pick_batch_prec(int prec, int r, bool range)
+{
+    if (prec == 1) return pick_batch_f16_entry(r, range);
+    if (prec == 2) return pick_batch_bf16_entry(r, range);
+    return pick_batch_f32_entry(r, range);
+}
+
 namespace {
 
-constexpr int kTW = 32;          // tile width  (one warp across)
-constexpr int kTH = 32;          // tile height
-constexpr int kStrip = 8;        // pixels per thread (vertical strip)
-constexpr int kThreads = kTW * kTH / kStrip;  // 128
-constexpr int kMaxTemplR = 16;
-constexpr int kMaxTiledR = 48;
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2_approx(float x)
+// ---------------------------------------------------------------------------------------------
+// Radii above kMaxTemplR: scalar FP32 tiles with a runtime window (one shared load per tap).
+// ---------------------------------------------------------------------------------------------
+template <bool RANGE>
+__global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __restrict__ img,
+                                                               float* __restrict__ ex,
+                                                               float* __restrict__ ey, int H,
+                                                               int W, int R, int th, float kappa,
+                                                               float inv_kappa, float cs)
 {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ int wrap_idx(int i, int n)
-{
-    int m = i % n;
-    return m < 0 ? m + n : m;
-}
-
-// Shared-memory layout of a tile for radius R: f on (TH+2R+1) x (TW+2R+1), then g_x, g_y on
-// (TH+2R) x (TW+2R).
-__host__ __device__ __forceinline__ int f_pitch(int R) { return kTW + 2 * R + 1; }
-__host__ __device__ __forceinline__ int g_pitch(int R) { return kTW + 2 * R; }
-__host__ __device__ __forceinline__ size_t tile_smem_bytes(int R)
-{
-    return sizeof(float) * ((size_t)(kTH + 2 * R + 1) * f_pitch(R) +
-                            2 * (size_t)(kTH + 2 * R) * g_pitch(R));
-}
-
-// Load the periodic tile and form kappa * gradients.  Returns pointers into shared memory.
-__device__ __forceinline__ void load_tile_gradients(const float* __restrict__ f, int H, int W,
-                                                    int x0, int y0, int R, float kappa,
-                                                    float* sm, float*& gx, float*& gy)
-{
-    const int fp = f_pitch(R), fr = kTH + 2 * R + 1;
-    const int gp = g_pitch(R), gr = kTH + 2 * R;
-    float* sf = sm;
-    gx = sm + fr * fp;
-    gy = gx + gr * gp;
-    for (int i = threadIdx.x; i < fr * fp; i += blockDim.x) {
-        const int r = i / fp, c = i - r * fp;
-        const int yy = wrap_idx(y0 - R + r, H), xx = wrap_idx(x0 - R + c, W);
-        sf[i] = __ldg(f + (size_t)yy * W + xx);
-    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int fp = f_pitch(R), gp = g_pitch(R), gr = g_rows(R, th);
+    float* sf = reinterpret_cast<float*>(smem);
+    float* gx = reinterpret_cast<float*>(smem + f_bytes(R, th));
+    float* gy = gx + gr * gp;
+    const size_t plane = (size_t)H * W;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * th;
+    load_f_tile(img + blockIdx.z * plane, H, W, x0, y0, R, th, sf);
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        const float v = sf[r * fp + c];
-        gx[i] = kappa * (sf[r * fp + c + 1] - v);
-        gy[i] = kappa * (sf[(r + 1) * fp + c] - v);
+        gx[i] = grad_x(sf, fp, r, c, kappa);
+        gy[i] = grad_y(sf, fp, r, c, kappa);
     }
     __syncthreads();
-}
-
-__device__ __forceinline__ void store_residuals(float* __restrict__ ex, float* __restrict__ ey,
-                                                int H, int W, int x, int ybase,
-                                                const float (&ax)[kStrip], const float (&zx)[kStrip],
-                                                const float (&sx)[kStrip], const float (&ay)[kStrip],
-                                                const float (&zy)[kStrip], const float (&sy)[kStrip],
-                                                float inv_kappa)
-{
-    if (x >= W) return;
-#pragma unroll
-    for (int j = 0; j < kStrip; ++j) {
-        const int y = ybase + j;
-        if (y < H) {
-            ex[(size_t)y * W + x] = (__fdiv_rn(ax[j], zx[j]) - sx[j]) * inv_kappa;
-            ey[(size_t)y * W + x] = (__fdiv_rn(ay[j], zy[j]) - sy[j]) * inv_kappa;
-        }
-    }
-}
-
-// Tiled kernel, window fully unrolled per column for a compile-time radius R.
-template <int R, bool RANGE>
-__global__ void __launch_bounds__(kThreads) k1_blf_tiled(const float* __restrict__ img,
-                                                         float* __restrict__ ex,
-                                                         float* __restrict__ ey, int H, int W,
-                                                         float kappa, float inv_kappa, float cs)
-{
-    extern __shared__ float sm[];
-    const size_t plane = (size_t)H * W;
-    const float* f = img + blockIdx.z * plane;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    float *gx, *gy;
-    load_tile_gradients(f, H, W, x0, y0, R, kappa, sm, gx, gy);
-
-    constexpr int gp = kTW + 2 * R;
-    const int cx = threadIdx.x & (kTW - 1);
-    const int r0 = (threadIdx.x / kTW) * kStrip;
-    float sx[kStrip], sy[kStrip], ax[kStrip], ay[kStrip], zx[kStrip], zy[kStrip];
-#pragma unroll
-    for (int j = 0; j < kStrip; ++j) {
-        sx[j] = gx[(R + r0 + j) * gp + R + cx];
-        sy[j] = gy[(R + r0 + j) * gp + R + cx];
-        ax[j] = ay[j] = zx[j] = zy[j] = 0.f;
-    }
-    // spatial log2-weights: a(dx, dy) = -(dx^2 + dy^2) * cs
-    float sa[2 * R + 1];
-#pragma unroll
-    for (int d = 0; d <= 2 * R; ++d) sa[d] = -float((d - R) * (d - R)) * cs;
-
-#pragma unroll 1
-    for (int dx = -R; dx <= R; ++dx) {
-        const float adx = -float(dx * dx) * cs;
-        float ra[2 * R + 1];
-#pragma unroll
-        for (int d = 0; d <= 2 * R; ++d) ra[d] = adx + sa[d];
-        const float* colx = gx + r0 * gp + R + cx + dx;
-        const float* coly = gy + r0 * gp + R + cx + dx;
-#pragma unroll
-        for (int i = 0; i < kStrip + 2 * R; ++i) {
-            const float tx = colx[i * gp];
-            const float ty = coly[i * gp];
-#pragma unroll
-            for (int j = 0; j < kStrip; ++j) {
-                const int d = i - j;  // dy + R
-                if (d < 0 || d > 2 * R) continue;
-                float wx, wy;
-                if (RANGE) {
-                    const float qx = tx - sx[j];
-                    const float qy = ty - sy[j];
-                    wx = ex2_approx(fmaf(-qx, qx, ra[d]));
-                    wy = ex2_approx(fmaf(-qy, qy, ra[d]));
-                } else {
-                    wx = wy = ex2_approx(ra[d]);
-                }
-                ax[j] = fmaf(wx, tx, ax[j]);
-                zx[j] += wx;
-                ay[j] = fmaf(wy, ty, ay[j]);
-                zy[j] += wy;
-            }
-        }
-    }
-    store_residuals(ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W, x0 + cx, y0 + r0,
-                    ax, zx, sx, ay, zy, sy, inv_kappa);
-}
-
-// Tiled kernel with a runtime radius (kMaxTemplR < R <= kMaxTiledR): one shared-memory read per
-// tap instead of register reuse across the strip.
-template <bool RANGE>
-__global__ void __launch_bounds__(kThreads) k1_blf_tiled_rt(const float* __restrict__ img,
-                                                            float* __restrict__ ex,
-                                                            float* __restrict__ ey, int H, int W,
-                                                            int R, float kappa, float inv_kappa,
-                                                            float cs)
-{
-    extern __shared__ float sm[];
-    const size_t plane = (size_t)H * W;
-    const float* f = img + blockIdx.z * plane;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    float *gx, *gy;
-    load_tile_gradients(f, H, W, x0, y0, R, kappa, sm, gx, gy);
-    const int gp = g_pitch(R);
     const int cx = threadIdx.x & (kTW - 1);
     const int r0 = (threadIdx.x / kTW) * kStrip;
     float sx[kStrip], sy[kStrip], ax[kStrip], ay[kStrip], zx[kStrip], zy[kStrip];
@@ -207,8 +86,8 @@ __global__ void __launch_bounds__(kThreads) k1_blf_tiled_rt(const float* __restr
             }
         }
     }
-    store_residuals(ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W, x0 + cx, y0 + r0,
-                    ax, zx, sx, ay, zy, sy, inv_kappa);
+    store_strip(ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W, x0 + cx, y0 + r0, ax, zx,
+                sx, ay, zy, sy, inv_kappa);
 }
 
 // Radii above the tiled limit: gradients precomputed to global memory, one pixel per thread.
@@ -216,15 +95,14 @@ __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ 
                              float kappa)
 {
     const size_t plane = (size_t)H * W;
-    const float* f = img + blockIdx.y * plane;
-    float* gx = g + blockIdx.y * 2 * plane;
-    float* gy = gx + plane;
+    float* gx = g;
+    float* gy = g + plane;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = int(i / W), x = int(i - (size_t)y * W);
-        const float v = f[i];
-        gx[i] = kappa * (f[(size_t)y * W + (x + 1 == W ? 0 : x + 1)] - v);
-        gy[i] = kappa * (f[(size_t)(y + 1 == H ? 0 : y + 1) * W + x] - v);
+        const float v = img[i];
+        gx[i] = kappa * (img[(size_t)y * W + (x + 1 == W ? 0 : x + 1)] - v);
+        gy[i] = kappa * (img[(size_t)(y + 1 == H ? 0 : y + 1) * W + x] - v);
     }
 }
 
@@ -234,8 +112,8 @@ __global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ e
                               float cs)
 {
     const size_t plane = (size_t)H * W;
-    const float* gx = g + blockIdx.y * 2 * plane;
-    const float* gy = gx + plane;
+    const float* gx = g;
+    const float* gy = g + plane;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = int(i / W), x = int(i - (size_t)y * W);
@@ -261,25 +139,24 @@ __global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ e
                 zy += wy;
             }
         }
-        ex[blockIdx.y * plane + i] = (__fdiv_rn(ax, zx) - sx) * inv_kappa;
-        ey[blockIdx.y * plane + i] = (__fdiv_rn(ay, zy) - sy) * inv_kappa;
+        ex[i] = (__fdiv_rn(ax, zx) - sx) * inv_kappa;
+        ey[i] = (__fdiv_rn(ay, zy) - sy) * inv_kappa;
     }
 }
 
-using TiledFn = void (*)(const float*, float*, float*, int, int, float, float, float);
-
-template <int R>
-TiledFn pick_tiled(int r, bool range)
-{
-    if constexpr (R > kMaxTemplR) {
-        return nullptr;
-    } else {
-        if (r == R) return range ? k1_blf_tiled<R, true> : k1_blf_tiled<R, false>;
-        return pick_tiled<R + 1>(r, range);
-    }
-}
 
 }  // namespace
+
+size_t blf_templ_smem_bytes(int R, int prec, int th)
+{
+    if (prec == 1) return tile_smem_bytes(R, sizeof(__half2), th);
+    return tile_smem_bytes(R, sizeof(float2), th);
+}
+
+int blf_tile_height(int th)
+{
+    return (th == 8 || th == 16 || th == 32 || th == 64) ? th : 32;
+}
 
 int blf_tiled_max_radius() { return kMaxTiledR; }
 
@@ -287,48 +164,90 @@ void init_blf_kernel_attributes()
 {
     for (int r = 0; r <= kMaxTemplR; ++r)
         for (int range = 0; range < 2; ++range)
-            cudaFuncSetAttribute(pick_tiled<0>(r, range), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem_bytes(r));
-    cudaFuncSetAttribute(k1_blf_tiled_rt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_smem_bytes(kMaxTiledR));
-    cudaFuncSetAttribute(k1_blf_tiled_rt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_smem_bytes(kMaxTiledR));
+            for (int prec = 0; prec < 3; ++prec) {
+                cudaFuncSetAttribute(pick_tiled_prec(prec, r, range),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)blf_templ_smem_bytes(r, prec, kMaxTH));
+                cudaFuncSetAttribute(pick_batch_prec(prec, r, range),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)blf_templ_smem_bytes(r, prec, kMaxTH));
+            }
+    const int rt = (int)tile_smem_bytes(kMaxTiledR, sizeof(float), 32);
+    cudaFuncSetAttribute(k1_blf_tiled_rt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rt);
+    cudaFuncSetAttribute(k1_blf_tiled_rt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rt);
+}
+
+void blf_constants(float sigma_s, float sigma_r, float* kappa, float* inv_kappa, float* cs)
+{
+    const bool range = std::isfinite(sigma_r);
+    const double kappa_d = range ? std::sqrt(1.4426950408889634 / (2.0 * (double)sigma_r * sigma_r)) : 1.0;
+    *kappa = (float)kappa_d;
+    *inv_kappa = (float)(1.0 / kappa_d);
+    *cs = std::isfinite(sigma_s) ? (float)(1.4426950408889634 / (2.0 * (double)sigma_s * sigma_s))
+                                 : 0.0f;
 }
 
 cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, const BlfParams& p,
                                 float* gscratch, cudaStream_t s)
 {
     const bool range = std::isfinite(p.sigma_r);
-    const double kappa_d = range ? std::sqrt(1.4426950408889634 / (2.0 * (double)p.sigma_r * p.sigma_r)) : 1.0;
-    const float kappa = (float)kappa_d;
-    const float inv_kappa = (float)(1.0 / kappa_d);
-    const float cs = std::isfinite(p.sigma_s)
-                         ? (float)(1.4426950408889634 / (2.0 * (double)p.sigma_s * p.sigma_s))
-                         : 0.0f;
+    float kappa, inv_kappa, cs;
+    blf_constants(p.sigma_s, p.sigma_r, &kappa, &inv_kappa, &cs);
     const int R = p.radius;
     if (R <= kMaxTiledR) {
-        dim3 grid((p.W + kTW - 1) / kTW, (p.H + kTH - 1) / kTH, C);
-        const size_t smem = tile_smem_bytes(R);
+        const int th = (R <= kMaxTemplR) ? blf_tile_height(p.tile_h) : 32;
+        const int threads = kTW * th / kStrip;
+        dim3 grid((p.W + kTW - 1) / kTW, (p.H + th - 1) / th, C);
         if (R <= kMaxTemplR) {
-            TiledFn fn = pick_tiled<0>(R, range);
-            fn<<<grid, kThreads, smem, s>>>(img, ex, ey, p.H, p.W, kappa, inv_kappa, cs);
-        } else if (range) {
-            k1_blf_tiled_rt<true><<<grid, kThreads, smem, s>>>(img, ex, ey, p.H, p.W, R, kappa, inv_kappa, cs);
+            TiledFn fn = pick_tiled_prec(p.prec, R, range);
+            fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th), s>>>(img, ex, ey, p.H, p.W, th,
+                                                                         kappa, inv_kappa, cs);
         } else {
-            k1_blf_tiled_rt<false><<<grid, kThreads, smem, s>>>(img, ex, ey, p.H, p.W, R, kappa, inv_kappa, cs);
+            if (p.prec != 0) return cudaErrorNotSupported;
+            const size_t smem = tile_smem_bytes(R, sizeof(float), th);
+            if (range)
+                k1_blf_tiled_rt<true><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, kappa, inv_kappa, cs);
+            else
+                k1_blf_tiled_rt<false><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, kappa, inv_kappa, cs);
         }
         return cudaGetLastError();
     }
+    if (p.prec != 0) return cudaErrorNotSupported;
     if (!gscratch) return cudaErrorInvalidValue;
     const size_t plane = (size_t)p.H * p.W;
     const int blocks = (int)std::min<size_t>((plane + 255) / 256, 4096);
     for (int c = 0; c < C; ++c) {
-        k1_gradients<<<dim3(blocks, 1), 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kappa);
+        k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kappa);
         if (range)
-            k1_blf_global<true><<<dim3(blocks, 1), 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
         else
-            k1_blf_global<false><<<dim3(blocks, 1), 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
     }
+    return cudaGetLastError();
+}
+
+int blf_batch_max_radius() { return kMaxTemplR; }
+
+void blf_tiles(int H, int W, int th, int* tiles_x, int* tiles_y)
+{
+    th = blf_tile_height(th);
+    *tiles_x = (W + kTW - 1) / kTW;
+    *tiles_y = (H + th - 1) / th;
+}
+
+cudaError_t launch_blf_batch(const BatchJob* jobs, const int2* grp, int ngrp, int total, int radius,
+                             bool range, int prec, int th, int num_sms, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    BatchFn fn = pick_batch_prec(prec, radius, range);
+    if (!fn) return cudaErrorNotSupported;
+    th = blf_tile_height(th);
+    const int threads = kTW * th / kStrip;
+    const size_t smem = blf_templ_smem_bytes(radius, prec, th);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    const int grid = std::max(1, std::min(total, num_sms * std::max(occ, 1)));
+    fn<<<grid, threads, smem, s>>>(jobs, grp, ngrp, total);
     return cudaGetLastError();
 }
 

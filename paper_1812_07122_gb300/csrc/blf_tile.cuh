@@ -1,0 +1,502 @@
+// Shared device code of step 1 of BLF-LS (Section III-A): the bilateral filter of Eq. 1 on the periodic forward-
+// difference gradients (Section II-B), emitted as residuals e_* = f_BLF(g_*) - g_*.
+//
+// K1 (tiled): one CTA per 32x32 output tile of one channel, 128 threads.  The CTA loads the
+// image tile with an (r+1)-pixel periodic halo into shared memory and forms both gradient fields
+// on the tile + r halo, pre-scaled by kappa = sqrt(log2(e) / (2 sigma_r^2)) so that a range
+// weight is a single exp2(-(t' - s')^2).  Each value is stored twice side by side, (g', g'), so
+// one 64-bit shared load feeds a packed pair of pixels.  Each thread filters a vertical strip of
+// 8 pixels (4 pairs) of both fields: for every window column dx it streams the 8 + 2r values of
+// that column once and applies each to every pair in reach.  The spatial weight is split as
+// exp2(a_dx) * exp2(a_dy): the dy part sits in the exponent (a per-kernel register table), the
+// dx part multiplies the tap value once per row.  Per pair of taps the FP32 form issues one
+// packed subtract, one packed FMA (the exponent), two MUFU ex2 and two packed FMAs (sum of
+// weighted values and sum of weights) -- three instructions per tap.
+//
+// Precision forms (same tiling):
+//   FP16W: tiles, exponent, weights and products in half2 (ex2.approx.f16x2 gives two weights per
+//          MUFU operation); the products and weights of one window column are summed in half2
+//          and flushed into FP32 accumulators (scaled by exp2(a_dx)) after every column.
+//   BF16W: exponent in FP32 (packed), weights rounded to BF16 by ex2.approx.ftz.bf16x2, then
+//          widened (exactly) to FP32 for the products and sums.
+// Radii up to kMaxTemplR are compiled with the window unrolled per column; larger radii up to
+// kMaxTiledR use a scalar FP32 kernel with a runtime window; above that a per-pixel kernel reads
+// precomputed gradients from global memory.
+#pragma once
+#include "internal.h"
+
+#include <cmath>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace blfls {
+namespace {
+
+constexpr int kTW = 32;          // tile width  (one warp across)
+constexpr int kMaxTH = 64;       // tallest tile (rows); the height is a launch parameter
+constexpr int kStrip = 8;        // pixels per thread (vertical strip)
+constexpr int kPairs = kStrip / 2;
+constexpr int kMaxThreads = kTW * kMaxTH / kStrip;  // 256: 32 threads per 8 rows
+constexpr int kMaxTemplR = 16;
+constexpr int kMaxTiledR = 48;
+constexpr float kBig = 1e30f;    // exponent offset that turns a weight into exactly 0
+
+using u64 = unsigned long long;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ __half2 ex2_h2(__half2 x)
+{
+    unsigned xi = *reinterpret_cast<unsigned*>(&x), yi;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(yi) : "r"(xi));
+    return *reinterpret_cast<__half2*>(&yi);
+}
+__device__ __forceinline__ __nv_bfloat162 ex2_bf2(__nv_bfloat162 x)
+{
+    unsigned xi = *reinterpret_cast<unsigned*>(&x), yi;
+    asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(yi) : "r"(xi));
+    return *reinterpret_cast<__nv_bfloat162*>(&yi);
+}
+// packed FP32 pairs (sm_100+ f32x2 arithmetic)
+__device__ __forceinline__ u64 pk(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(u64 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n)
+{
+    int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// Shared-memory layout of a tile for radius R: f on (TH+2R+1) x (TW+2R+1) floats, then the two
+// gradient tiles of (TH+2R) x (TW+2R) elements of `elem` bytes each.
+__host__ __device__ __forceinline__ int f_pitch(int R) { return kTW + 2 * R + 1; }
+__host__ __device__ __forceinline__ int f_rows(int R, int th) { return th + 2 * R + 1; }
+__host__ __device__ __forceinline__ int g_pitch(int R) { return kTW + 2 * R; }
+__host__ __device__ __forceinline__ int g_rows(int R, int th) { return th + 2 * R; }
+__host__ __device__ __forceinline__ size_t f_bytes(int R, int th)
+{
+    return ((sizeof(float) * (size_t)f_rows(R, th) * f_pitch(R)) + 15) & ~size_t(15);
+}
+__host__ __device__ __forceinline__ size_t tile_smem_bytes(int R, size_t elem, int th)
+{
+    return f_bytes(R, th) + 2 * elem * (size_t)g_rows(R, th) * g_pitch(R);
+}
+
+__device__ __forceinline__ void load_f_tile(const float* __restrict__ f, int H, int W, int x0,
+                                            int y0, int R, int th, float* sf)
+{
+    const int fp = f_pitch(R), fr = f_rows(R, th);
+    for (int i = threadIdx.x; i < fr * fp; i += blockDim.x) {
+        const int r = i / fp, c = i - r * fp;
+        const int yy = wrap_idx(y0 - R + r, H), xx = wrap_idx(x0 - R + c, W);
+        sf[i] = __ldg(f + (size_t)yy * W + xx);
+    }
+}
+
+// kappa-scaled gradient at tile position (r, c) of the g tiles (FP32, from the f tile)
+__device__ __forceinline__ float grad_x(const float* sf, int fp, int r, int c, float kappa)
+{
+    return kappa * (sf[r * fp + c + 1] - sf[r * fp + c]);
+}
+__device__ __forceinline__ float grad_y(const float* sf, int fp, int r, int c, float kappa)
+{
+    return kappa * (sf[(r + 1) * fp + c] - sf[r * fp + c]);
+}
+
+// e = (acc / Z - s') / kappa for the strip (FP32 accumulators), guarded against the image edge.
+__device__ __forceinline__ void store_strip(float* __restrict__ ex, float* __restrict__ ey, int H,
+                                            int W, int x, int ybase, const float* ax,
+                                            const float* zx, const float* sx, const float* ay,
+                                            const float* zy, const float* sy, float inv_kappa)
+{
+    if (x >= W) return;
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        const int y = ybase + j;
+        if (y < H) {
+            ex[(size_t)y * W + x] = (__fdiv_rn(ax[j], zx[j]) - sx[j]) * inv_kappa;
+            ey[(size_t)y * W + x] = (__fdiv_rn(ay[j], zy[j]) - sy[j]) * inv_kappa;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32, packed f32x2
+// ---------------------------------------------------------------------------------------------
+template <int R, bool RANGE>
+__device__ __forceinline__ void tile_f32(const float* __restrict__ f, float* __restrict__ ex,
+                                          float* __restrict__ ey, int H, int W, int x0,
+                                          int y0, int th, float kappa, float inv_kappa,
+                                          float cs, unsigned char* smem)
+{
+    constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
+    const int gr = th + 2 * R;
+    float* sf = reinterpret_cast<float*>(smem);
+    float2* gx = reinterpret_cast<float2*>(smem + f_bytes(R, th));
+    float2* gy = gx + gr * gp;
+    load_f_tile(f, H, W, x0, y0, R, th, sf);
+    __syncthreads();
+    for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
+        const int r = i / gp, c = i - r * gp;
+        const float vx = grad_x(sf, fp, r, c, kappa), vy = grad_y(sf, fp, r, c, kappa);
+        gx[i] = make_float2(vx, vx);
+        gy[i] = make_float2(vy, vy);
+    }
+    __syncthreads();
+
+    const int cx = threadIdx.x & (kTW - 1);
+    const int r0 = (threadIdx.x / kTW) * kStrip;
+    float sxs[kStrip], sys[kStrip];
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        sxs[j] = gx[(R + r0 + j) * gp + R + cx].x;
+        sys[j] = gy[(R + r0 + j) * gp + R + cx].x;
+    }
+    u64 SX[kPairs], SY[kPairs], AX[kPairs], AY[kPairs], ZX[kPairs], ZY[kPairs];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        SX[p] = pk(sxs[2 * p], sxs[2 * p + 1]);
+        SY[p] = pk(sys[2 * p], sys[2 * p + 1]);
+        AX[p] = AY[p] = ZX[p] = ZY[p] = 0ull;
+    }
+    // NA[k] = (n(k), n(k-1)) with n(d) = (d-R)^2 cs for d in [0, 2R], kBig outside the window
+    u64 NA[2 * R + 2];
+#pragma unroll
+    for (int k = 0; k <= 2 * R + 1; ++k) {
+        const float lo = (k <= 2 * R) ? float((k - R) * (k - R)) * cs : kBig;
+        const float hi = (k >= 1) ? float((k - 1 - R) * (k - 1 - R)) * cs : kBig;
+        NA[k] = pk(lo, hi);
+        asm volatile("" : "+l"(NA[k]));   // keep the table in registers (no per-use recompute)
+    }
+
+#pragma unroll 1
+    for (int dx = -R; dx <= R; ++dx) {
+        const float gdx = ex2_approx(-float(dx * dx) * cs);
+        const u64 GD = pk(gdx, gdx);
+        const u64* colx = reinterpret_cast<const u64*>(gx + r0 * gp + R + cx + dx);
+        const u64* coly = reinterpret_cast<const u64*>(gy + r0 * gp + R + cx + dx);
+#pragma unroll
+        for (int i = 0; i < kStrip + 2 * R; ++i) {
+            const u64 TX = colx[i * gp], TY = coly[i * gp];
+            const u64 TGX = mul2(TX, GD), TGY = mul2(TY, GD);
+#pragma unroll
+            for (int p = 0; p < kPairs; ++p) {
+                const int k = i - 2 * p;
+                if (k < 0 || k > 2 * R + 1) continue;
+                float a0, a1, b0, b1;
+                if (RANGE) {
+                    const u64 QX = sub2(TX, SX[p]), QY = sub2(TY, SY[p]);
+                    upk(fma2(QX, QX, NA[k]), a0, a1);
+                    upk(fma2(QY, QY, NA[k]), b0, b1);
+                } else {
+                    upk(NA[k], a0, a1);
+                    b0 = a0;
+                    b1 = a1;
+                }
+                const u64 WX = pk(ex2_approx(-a0), ex2_approx(-a1));
+                const u64 WY = pk(ex2_approx(-b0), ex2_approx(-b1));
+                AX[p] = fma2(WX, TGX, AX[p]);
+                ZX[p] = fma2(WX, GD, ZX[p]);
+                AY[p] = fma2(WY, TGY, AY[p]);
+                ZY[p] = fma2(WY, GD, ZY[p]);
+            }
+        }
+    }
+    float ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        upk(AX[p], ax[2 * p], ax[2 * p + 1]);
+        upk(ZX[p], zx[2 * p], zx[2 * p + 1]);
+        upk(AY[p], ay[2 * p], ay[2 * p + 1]);
+        upk(ZY[p], zy[2 * p], zy[2 * p + 1]);
+    }
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
+                sxs, ay, zy, sys, inv_kappa);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP16 weights: exponent, weights and products in half2; per-column sums flushed to FP32
+// ---------------------------------------------------------------------------------------------
+template <int R, bool RANGE>
+__device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __restrict__ ex,
+                                          float* __restrict__ ey, int H, int W, int x0,
+                                          int y0, int th, float kappa, float inv_kappa,
+                                          float cs, unsigned char* smem)
+{
+    constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
+    const int gr = th + 2 * R;
+    float* sf = reinterpret_cast<float*>(smem);
+    __half2* gx = reinterpret_cast<__half2*>(smem + f_bytes(R, th));
+    __half2* gy = gx + gr * gp;
+    load_f_tile(f, H, W, x0, y0, R, th, sf);
+    __syncthreads();
+    for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
+        const int r = i / gp, c = i - r * gp;
+        gx[i] = __float2half2_rn(grad_x(sf, fp, r, c, kappa));
+        gy[i] = __float2half2_rn(grad_y(sf, fp, r, c, kappa));
+    }
+    __syncthreads();
+
+    const int cx = threadIdx.x & (kTW - 1);
+    const int r0 = (threadIdx.x / kTW) * kStrip;
+    float sxs[kStrip], sys[kStrip], ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, kappa);   // FP32 centre values
+        sys[j] = grad_y(sf, fp, R + r0 + j, R + cx, kappa);
+        ax[j] = zx[j] = ay[j] = zy[j] = 0.f;
+    }
+    __half2 SX[kPairs], SY[kPairs];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        SX[p] = __lows2half2(gx[(R + r0 + 2 * p) * gp + R + cx], gx[(R + r0 + 2 * p + 1) * gp + R + cx]);
+        SY[p] = __lows2half2(gy[(R + r0 + 2 * p) * gp + R + cx], gy[(R + r0 + 2 * p + 1) * gp + R + cx]);
+    }
+    // A[k] = (a(k), a(k-1)), a(d) = -(d-R)^2 cs inside the window, -inf outside
+    __half2 A[2 * R + 2];
+#pragma unroll
+    for (int k = 0; k <= 2 * R + 1; ++k) {
+        const float lo = (k <= 2 * R) ? -float((k - R) * (k - R)) * cs : -INFINITY;
+        const float hi = (k >= 1) ? -float((k - 1 - R) * (k - 1 - R)) * cs : -INFINITY;
+        A[k] = __floats2half2_rn(lo, hi);
+        asm volatile("" : "+r"(*reinterpret_cast<unsigned*>(&A[k])));
+    }
+    const __half2 hz = __float2half2_rn(0.f);
+
+#pragma unroll 1
+    for (int dx = -R; dx <= R; ++dx) {
+        const float gdx = ex2_approx(-float(dx * dx) * cs);
+        __half2 PX[kPairs], PY[kPairs], QX[kPairs], QY[kPairs];   // partial sums of w t and w
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) PX[p] = PY[p] = QX[p] = QY[p] = hz;
+        const __half2* colx = gx + r0 * gp + R + cx + dx;
+        const __half2* coly = gy + r0 * gp + R + cx + dx;
+#pragma unroll
+        for (int i = 0; i < kStrip + 2 * R; ++i) {
+            const __half2 TX = colx[i * gp], TY = coly[i * gp];
+#pragma unroll
+            for (int p = 0; p < kPairs; ++p) {
+                const int k = i - 2 * p;
+                if (k < 0 || k > 2 * R + 1) continue;
+                __half2 WX, WY;
+                if (RANGE) {
+                    const __half2 dX = __hsub2(TX, SX[p]), dY = __hsub2(TY, SY[p]);
+                    WX = ex2_h2(__hfma2(__hneg2(dX), dX, A[k]));
+                    WY = ex2_h2(__hfma2(__hneg2(dY), dY, A[k]));
+                } else {
+                    WX = WY = ex2_h2(A[k]);
+                }
+                PX[p] = __hfma2(WX, TX, PX[p]);
+                QX[p] = __hadd2(QX[p], WX);
+                PY[p] = __hfma2(WY, TY, PY[p]);
+                QY[p] = __hadd2(QY[p], WY);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+            const float2 px = __half22float2(PX[p]), qx = __half22float2(QX[p]);
+            const float2 py = __half22float2(PY[p]), qy = __half22float2(QY[p]);
+            ax[2 * p] = fmaf(gdx, px.x, ax[2 * p]);
+            ax[2 * p + 1] = fmaf(gdx, px.y, ax[2 * p + 1]);
+            zx[2 * p] = fmaf(gdx, qx.x, zx[2 * p]);
+            zx[2 * p + 1] = fmaf(gdx, qx.y, zx[2 * p + 1]);
+            ay[2 * p] = fmaf(gdx, py.x, ay[2 * p]);
+            ay[2 * p + 1] = fmaf(gdx, py.y, ay[2 * p + 1]);
+            zy[2 * p] = fmaf(gdx, qy.x, zy[2 * p]);
+            zy[2 * p + 1] = fmaf(gdx, qy.y, zy[2 * p + 1]);
+        }
+    }
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
+                sxs, ay, zy, sys, inv_kappa);
+}
+
+// ---------------------------------------------------------------------------------------------
+// BF16 weights: exponent in packed FP32, weights by ex2.approx.ftz.bf16x2, widened back to FP32
+// (exact) for the products and sums, which stay in packed FP32.  Same tiles as the FP32 form.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ u64 bf2_to_f2(__nv_bfloat162 w)
+{
+    const unsigned b = *reinterpret_cast<unsigned*>(&w);
+    return pk(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
+}
+
+template <int R, bool RANGE>
+__device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __restrict__ ex,
+                                          float* __restrict__ ey, int H, int W, int x0,
+                                          int y0, int th, float kappa, float inv_kappa,
+                                          float cs, unsigned char* smem)
+{
+    constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
+    const int gr = th + 2 * R;
+    float* sf = reinterpret_cast<float*>(smem);
+    float2* gx = reinterpret_cast<float2*>(smem + f_bytes(R, th));
+    float2* gy = gx + gr * gp;
+    load_f_tile(f, H, W, x0, y0, R, th, sf);
+    __syncthreads();
+    for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
+        const int r = i / gp, c = i - r * gp;
+        const float vx = grad_x(sf, fp, r, c, kappa), vy = grad_y(sf, fp, r, c, kappa);
+        gx[i] = make_float2(vx, vx);
+        gy[i] = make_float2(vy, vy);
+    }
+    __syncthreads();
+
+    const int cx = threadIdx.x & (kTW - 1);
+    const int r0 = (threadIdx.x / kTW) * kStrip;
+    float sxs[kStrip], sys[kStrip];
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        sxs[j] = gx[(R + r0 + j) * gp + R + cx].x;
+        sys[j] = gy[(R + r0 + j) * gp + R + cx].x;
+    }
+    u64 SX[kPairs], SY[kPairs], AX[kPairs], AY[kPairs], ZX[kPairs], ZY[kPairs];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        SX[p] = pk(sxs[2 * p], sxs[2 * p + 1]);
+        SY[p] = pk(sys[2 * p], sys[2 * p + 1]);
+        AX[p] = AY[p] = ZX[p] = ZY[p] = 0ull;
+    }
+    u64 NA[2 * R + 2];
+#pragma unroll
+    for (int k = 0; k <= 2 * R + 1; ++k) {
+        const float lo = (k <= 2 * R) ? float((k - R) * (k - R)) * cs : kBig;
+        const float hi = (k >= 1) ? float((k - 1 - R) * (k - 1 - R)) * cs : kBig;
+        NA[k] = pk(lo, hi);
+        asm volatile("" : "+l"(NA[k]));
+    }
+
+#pragma unroll 1
+    for (int dx = -R; dx <= R; ++dx) {
+        const float gdx = ex2_approx(-float(dx * dx) * cs);
+        const u64 GD = pk(gdx, gdx);
+        const u64* colx = reinterpret_cast<const u64*>(gx + r0 * gp + R + cx + dx);
+        const u64* coly = reinterpret_cast<const u64*>(gy + r0 * gp + R + cx + dx);
+#pragma unroll
+        for (int i = 0; i < kStrip + 2 * R; ++i) {
+            const u64 TX = colx[i * gp], TY = coly[i * gp];
+            const u64 TGX = mul2(TX, GD), TGY = mul2(TY, GD);
+#pragma unroll
+            for (int p = 0; p < kPairs; ++p) {
+                const int k = i - 2 * p;
+                if (k < 0 || k > 2 * R + 1) continue;
+                float a0, a1, b0, b1;
+                if (RANGE) {
+                    const u64 QX = sub2(TX, SX[p]), QY = sub2(TY, SY[p]);
+                    upk(fma2(QX, QX, NA[k]), a0, a1);
+                    upk(fma2(QY, QY, NA[k]), b0, b1);
+                } else {
+                    upk(NA[k], a0, a1);
+                    b0 = a0;
+                    b1 = a1;
+                }
+                const u64 WX = bf2_to_f2(ex2_bf2(__floats2bfloat162_rn(-a0, -a1)));
+                const u64 WY = bf2_to_f2(ex2_bf2(__floats2bfloat162_rn(-b0, -b1)));
+                AX[p] = fma2(WX, TGX, AX[p]);
+                ZX[p] = fma2(WX, GD, ZX[p]);
+                AY[p] = fma2(WY, TGY, AY[p]);
+                ZY[p] = fma2(WY, GD, ZY[p]);
+            }
+        }
+    }
+    float ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        upk(AX[p], ax[2 * p], ax[2 * p + 1]);
+        upk(ZX[p], zx[2 * p], zx[2 * p + 1]);
+        upk(AY[p], ay[2 * p], ay[2 * p + 1]);
+        upk(ZY[p], zy[2 * p], zy[2 * p + 1]);
+    }
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
+                sxs, ay, zy, sys, inv_kappa);
+}
+
+template <int R, bool RANGE, int PREC>
+__device__ __forceinline__ void blf_tile(const float* f, float* ex, float* ey, int H, int W, int x0,
+                                         int y0, int th, float kappa, float inv_kappa, float cs,
+                                         unsigned char* smem)
+{
+    if constexpr (PREC == 1) tile_f16<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    else if constexpr (PREC == 2) tile_bf16<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    else tile_f32<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+}
+
+// One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.
+template <int R, bool RANGE, int PREC>
+__global__ void __launch_bounds__(kMaxThreads) k1_blf(const float* __restrict__ img,
+                                                      float* __restrict__ ex,
+                                                      float* __restrict__ ey, int H, int W,
+                                                      int th, float kappa, float inv_kappa,
+                                                      float cs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t plane = (size_t)H * W;
+    blf_tile<R, RANGE, PREC>(img + blockIdx.z * plane, ex + blockIdx.z * plane,
+                             ey + blockIdx.z * plane, H, W, blockIdx.x * kTW, blockIdx.y * th,
+                             th, kappa, inv_kappa, cs, smem);
+}
+
+// Batched form: a persistent grid walks every tile of every channel of the jobs of one
+// (radius, range kernel, precision) group.  grp[g] = (job index, first item of that job).
+template <int R, bool RANGE, int PREC>
+__global__ void __launch_bounds__(kMaxThreads) k1_blf_batch(const BatchJob* __restrict__ jobs,
+                                                         const int2* __restrict__ grp, int ngrp,
+                                                         int total)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int g = 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        while (g + 1 < ngrp && __ldg(&grp[g + 1].y) <= item) ++g;
+        const BatchJob& J = jobs[__ldg(&grp[g].x)];
+        const int local = item - __ldg(&grp[g].y);
+        const int per_plane = J.tiles_x * J.tiles_y;
+        const int c = local / per_plane, rem = local - c * per_plane;
+        const int ty = rem / J.tiles_x, tx = rem - ty * J.tiles_x;
+        const size_t plane = (size_t)J.H * J.W;
+        __syncthreads();   // the previous tile's readers are done with shared memory
+        blf_tile<R, RANGE, PREC>(J.src + c * plane, J.ex + c * plane, J.ey + c * plane, J.H, J.W,
+                                 tx * kTW, ty * J.tile_h, J.tile_h, J.kappa, J.inv_kappa, J.cs,
+                                 smem);
+    }
+}
+
+}  // namespace
+
+using TiledFn = void (*)(const float*, float*, float*, int, int, int, float, float, float);
+using BatchFn = void (*)(const BatchJob*, const int2*, int, int);
+
+// Kernel pointers of one precision (defined in blf_f32.cu, blf_f16.cu, blf_bf16.cu).
+TiledFn pick_tiled_prec(int prec, int r, bool range);
+BatchFn pick_batch_prec(int prec, int r, bool range);
+size_t blf_templ_smem_bytes(int R, int prec, int th);
+
+}  // namespace blfls

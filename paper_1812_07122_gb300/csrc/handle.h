@@ -1,0 +1,85 @@
+// The handle behind the C ABI, and host helpers shared by the API files (not part of the ABI).
+#pragma once
+
+#include "blfls.h"
+#include "internal.h"
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+namespace blfls {
+struct BatchState;   // batched executor state (batch.cu)
+void destroy_batch_state(BatchState* b);
+}
+
+struct blfls_handle {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+    int col_block = 4;
+    std::map<int, blfls::FftPlanHost> plans;
+    // scratch (device)
+    float* ex = nullptr;
+    float* ey = nullptr;
+    size_t e_cap = 0;  // floats per plane
+    float2* spec = nullptr;
+    size_t spec_cap = 0;  // complex values
+    float* gscratch = nullptr;
+    size_t g_cap = 0;
+    float* io = nullptr;  // device copies for blfls_smooth_host: img then out
+    size_t io_cap = 0;
+    // kernel timing (blfls_profile_begin / _end)
+    bool prof_on = false;
+    bool prof_overflow = false;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_next = 0;
+    std::vector<std::pair<int, std::pair<int, int>>> prof_spans;  // stage, (start, end) event
+    unsigned long long generation = 0;  // bumped whenever a scratch buffer is reallocated
+    // autotuned launch shapes (tune.cu): K1 tile height per (radius, precision), K3 column
+    // block per ceil(log2) of the column-transform length
+    std::map<std::pair<int, int>, int> tune_tile_h;
+    std::map<int, int> tune_col_block;
+    blfls::BatchState* batch = nullptr;
+};
+
+namespace blfls {
+
+// Make the handle's device current for the duration of a call and restore the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+bool budget_allows(blfls_handle* h, size_t extra);
+// Grow a device buffer to `need` bytes within the handle's budget (contents are not kept).
+int grow_bytes(blfls_handle* h, void** ptr, size_t* cap_bytes, size_t need, const char* what);
+int get_plan(blfls_handle* h, int N, const FftPlanDev** out);
+int check_image_args(const void* a, const void* b, int H, int W, int C);
+int check_blf_args(int H, int W, float sigma_s, float sigma_r, int radius, int prec);
+int check_lambda(float lambda);
+int run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C, float lambda,
+               float sigma_s, float sigma_r, int radius, int iters, int prec, cudaStream_t s);
+int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t s);
+// Size the handle's batched-executor scratch arena up front (no reallocation later).
+int reserve_batch_scratch(blfls_handle* h, size_t bytes);
+int tuned_tile_h(const blfls_handle* h, int radius, int prec);
+int tuned_col_block(const blfls_handle* h, int L);
+int load_tune_table(blfls_handle* h, const char* path);
+int save_tune_table(const blfls_handle* h, const char* path);
+
+}  // namespace blfls

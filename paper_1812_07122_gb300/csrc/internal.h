@@ -55,13 +55,32 @@ FftPlanDev bind_fft_tables(const FftPlanDev& rel, const void* base);
 void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------------------------------------
+// Batched form: one entry per job of the device job table of one pass.
+// ---------------------------------------------------------------------------------------------
+struct BatchJob {
+    const float* src;   // this pass's input  [C][H][W]
+    float* dst;         // this pass's output [C][H][W]
+    float* ex;          // residual planes [C][H][W] (scratch)
+    float* ey;
+    float2* spec;       // half spectra [C][H][W/2+1] (scratch)
+    int H, W, C, radius;
+    float kappa, inv_kappa, cs;   // bilateral constants (see launch_blf_residual)
+    float lam, scale;             // solve: lambda and 1/(H W)
+    int lgc;                      // log2 of the column block of K3
+    int tiles_x, tiles_y;         // K1 tiling
+    int tile_h;                   // K1 tile height (rows)
+    FftPlanDev rp, cp;            // row (length W) and column (length H) plans
+};
+
+// ---------------------------------------------------------------------------------------------
 // Bilateral step (K1): for each channel, ex = BLF(D_x f) - D_x f and ey likewise.
 // ---------------------------------------------------------------------------------------------
 struct BlfParams {
     int H, W;
     int radius;
     float sigma_s, sigma_r;
-    int prec;  // blfls_precision
+    int prec;    // blfls_precision
+    int tile_h;  // K1 tile height: 8, 16, 32 or 64 rows (others select 32)
 };
 
 // Launch K1 over channels [0, C) of img (planes of H*W floats).  `gscratch` must hold
@@ -72,6 +91,15 @@ void init_solve_kernel_attributes();
 cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C,
                                 const BlfParams& p, float* gscratch, cudaStream_t s);
 int blf_tiled_max_radius();
+int blf_batch_max_radius();
+void blf_tiles(int H, int W, int tile_h, int* tiles_x, int* tiles_y);
+int blf_tile_height(int tile_h);   // the height actually used for a requested one
+// Bilateral constants of a job: kappa = sqrt(log2 e / (2 sigma_r^2)) (1 without range kernel),
+// cs = log2 e / (2 sigma_s^2) (0 without spatial kernel).
+void blf_constants(float sigma_s, float sigma_r, float* kappa, float* inv_kappa, float* cs);
+// Persistent K1 over the jobs of one (radius, range, precision) group; grp[g] = (job, first item).
+cudaError_t launch_blf_batch(const BatchJob* jobs, const int2* grp, int ngrp, int total, int radius,
+                             bool range, int prec, int tile_h, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // Fourier solve (K2 rows forward, K3 columns forward / divide / inverse, K4 rows inverse).
@@ -92,5 +120,15 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
 // Smallest/largest shared memory the solve kernels need for these plans (bytes).
 size_t solve_smem_rows(const FftPlanDev& rowp);
 size_t solve_smem_cols(const FftPlanDev& colp, int col_block);
+// Largest column block (log2) whose data fits the K3 shared-memory cap for a plan of length L.
+int solve_fit_lgc(int L, int col_block);
+
+// Batched solve phases: persistent grids over the row pairs (K2, K4) or column blocks (K3) of
+// every channel of every job; grp arrays as for launch_blf_batch.  smem_* = the largest dynamic
+// shared memory any job needs in that phase.
+cudaError_t launch_solve_batch(const BatchJob* jobs, int njobs, const int2* grp_rows,
+                               int total_rows, const int2* grp_cols, int total_cols,
+                               size_t smem_rows, size_t smem_cols, int num_sms, cudaStream_t s,
+                               const cudaEvent_t* marks = nullptr);
 
 }  // namespace blfls

@@ -177,13 +177,58 @@ def test_memory_budget_is_enforced():
         blfls.blfls_destroy(h2)
 
 
+TOL_HALF = 2e-3    # accuracy target of the FP16/BF16-weight forms (images in [0, 1])
+
+
+@pytest.mark.parametrize("prec", [blfls.BLFLS_FP16W, blfls.BLFLS_BF16W])
+@pytest.mark.parametrize("H,W,C,lam,ss,sr,r,iters", [
+    (96, 128, 3, 30.0, 5.0, 0.08, 10, 1),
+    (61, 97, 1, 50.0, 2.0, 0.05, 3, 2),
+    (256, 256, 1, 20.0, 3.0, 0.1, 5, 1),
+    (70, 66, 2, 1024.0, 8.0, 0.12, 16, 1),
+    (50, 70, 1, 20.0, 3.0, math.inf, 5, 1),
+])
+def test_precision_forms_match_oracle(h, prec, H, W, C, lam, ss, sr, r, iters):
+    f = _img(H, W, C, seed=C * 77 + W)
+    got = smooth(h, f, lam, ss, sr, r, iters, prec=prec)
+    want = oracle.blfls(f, lam, ss, sr, r, iters)
+    err = maxabs(got, want)
+    assert err <= TOL_HALF, err
+
+
+@pytest.mark.parametrize("prec", [blfls.BLFLS_FP16W, blfls.BLFLS_BF16W])
+def test_precision_forms_on_sharp_rectangles(h, prec):
+    """The 256x256 grey rectangles workload: gradients up to ~1 against sigma_r = 0.1 are the
+    hardest case for a half-precision exponent."""
+    f = synth.image_256_rectangles()
+    got = smooth(h, f, 20.0, 3.0, 0.1, 5, 1, prec=prec)
+    want = oracle.blfls(f, 20.0, 3.0, 0.1, 5, 1)
+    err = maxabs(got, want)
+    print(f"256x256 rectangles prec={prec}: max-abs {err:.3e}")
+    assert err <= TOL_HALF, err
+
+
+def test_precision_forms_reject_large_radius(h):
+    import torch
+    x = torch.zeros(1, 64, 64, device="cuda")
+    with pytest.raises(blfls.BlflsError) as ei:
+        blfls.blfls_smooth(h, x, x, 64, 64, 1, 10.0, 9.0, 0.1, 20, 1, blfls.BLFLS_FP16W)
+    assert ei.value.code == blfls.BLFLS_EINVAL
+
+
 def test_4k_rgb_three_iterations_full_image(h):
     """3840x2160 RGB, r = 10, sigma_s = 5, sigma_r = 0.08, lam = 30, 3 passes: every pixel of the
-    benchmark workload against the oracle (about a minute of FP64 work on the host cores)."""
+    benchmark workload against the oracle (about a minute of FP64 work on the host cores), for
+    the FP32 path (1e-4) and the FP16/BF16-weight forms (2e-3); per-channel errors printed."""
     f = synth.image_4k_rgb()
-    got = smooth(h, f, 30.0, 5.0, 0.08, 10, 3)
     want = oracle.blfls(f, 30.0, 5.0, 0.08, 10, 3)
-    err = maxabs(got, want)
-    rms = float(np.sqrt(np.mean((got.astype(np.float64) - want) ** 2)))
-    print(f"4K RGB x3: max-abs {err:.3e}, rms {rms:.3e}")
-    assert err <= TOL_FP32, err
+    for prec, tol, name in [(blfls.BLFLS_FP32, TOL_FP32, "fp32"),
+                            (blfls.BLFLS_FP16W, TOL_HALF, "fp16w"),
+                            (blfls.BLFLS_BF16W, TOL_HALF, "bf16w")]:
+        got = smooth(h, f, 30.0, 5.0, 0.08, 10, 3, prec=prec).astype(np.float64)
+        per_c = [(float(np.max(np.abs(got[c] - want[c]))),
+                  float(np.sqrt(np.mean((got[c] - want[c]) ** 2)))) for c in range(3)]
+        print(f"4K RGB x3 {name}: " + "; ".join(f"c{c} max-abs {m:.3e} rms {q:.3e}"
+                                                for c, (m, q) in enumerate(per_c)))
+        err = max(m for m, _ in per_c)
+        assert err <= tol, (name, err)
