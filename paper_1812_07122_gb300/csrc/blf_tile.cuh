@@ -1,24 +1,24 @@
 // Shared device code of step 1 of BLF-LS (Section III-A): the bilateral filter of Eq. 1 on the periodic forward-
 // difference gradients (Section II-B), emitted as residuals e_* = f_BLF(g_*) - g_*.
 //
-// K1 (tiled): one CTA per 32x32 output tile of one channel, 128 threads.  The CTA loads the
+// K1 (tiled): one CTA per 32 x th output tile of one channel (4 th threads).  The CTA loads the
 // image tile with an (r+1)-pixel periodic halo into shared memory and forms both gradient fields
 // on the tile + r halo, pre-scaled by kappa = sqrt(log2(e) / (2 sigma_r^2)) so that a range
-// weight is a single exp2(-(t' - s')^2).  Each value is stored twice side by side, (g', g'), so
-// one 64-bit shared load feeds a packed pair of pixels.  Each thread filters a vertical strip of
-// 8 pixels (4 pairs) of both fields: for every window column dx it streams the 8 + 2r values of
-// that column once and applies each to every pair in reach.  The spatial weight is split as
+// weight is a single exp2(-(t' - s')^2).  Each thread filters a vertical strip of 8 pixels of
+// both fields: for every window column dx it streams the 8 + 2r values of that column once and
+// applies each to every strip pixel in reach.  The spatial weight is split as
 // exp2(a_dx) * exp2(a_dy): the dy part sits in the exponent (a per-kernel register table), the
-// dx part multiplies the tap value once per row.  Per pair of taps the FP32 form issues one
-// packed subtract, one packed FMA (the exponent), two MUFU ex2 and two packed FMAs (sum of
+// dx part multiplies the tap value once per row.  The FP32 form packs the two gradient fields
+// into the two lanes of sm_100 f32x2 arithmetic (the tile stores (g_x', g_y') pairs): per tap pair
+// one packed subtract, one packed FMA (the exponent), two MUFU ex2 and two packed FMAs (sum of
 // weighted values and sum of weights) -- three instructions per tap.
 //
 // Precision forms (same tiling):
 //   FP16W: tiles, exponent, weights and products in half2 (ex2.approx.f16x2 gives two weights per
 //          MUFU operation); the products and weights of one window column are summed in half2
 //          and flushed into FP32 accumulators (scaled by exp2(a_dx)) after every column.
-//   BF16W: exponent in FP32 (packed), weights rounded to BF16 by ex2.approx.ftz.bf16x2, then
-//          widened (exactly) to FP32 for the products and sums.
+//   BF16W: as FP32 but the weights are rounded to BF16 by ex2.approx.ftz.bf16x2, then widened
+//          (exactly) to FP32 for the products and sums.
 // Radii up to kMaxTemplR are compiled with the window unrolled per column; larger radii up to
 // kMaxTiledR use a scalar FP32 kernel with a runtime window; above that a per-pixel kernel reads
 // precomputed gradients from global memory.
@@ -151,97 +151,109 @@ __device__ __forceinline__ void store_strip(float* __restrict__ ex, float* __res
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP32, packed f32x2
+// FP32 and BF16-weight forms, packed f32x2 with the two gradient fields in the two lanes: the
+// tile holds interleaved (g_x', g_y') pairs, so one 64-bit shared load gives both fields' value
+// of a tap, both lanes share the tap's spatial weight, and per tap pair the work is one packed
+// subtract, one packed FMA (exponent), two ex2, and two packed FMAs (weighted sum, weight sum).
+// BF16W rounds the weights to BF16 (ex2.approx.ftz.bf16x2) and widens them back exactly.
 // ---------------------------------------------------------------------------------------------
-template <int R, bool RANGE>
-__device__ __forceinline__ void tile_f32(const float* __restrict__ f, float* __restrict__ ex,
-                                          float* __restrict__ ey, int H, int W, int x0,
-                                          int y0, int th, float kappa, float inv_kappa,
-                                          float cs, unsigned char* smem)
+__device__ __forceinline__ u64 bf2_to_f2(__nv_bfloat162 w)
+{
+    const unsigned b = *reinterpret_cast<unsigned*>(&w);
+    return pk(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
+}
+
+template <int R, bool RANGE, bool BF16W>
+__device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
+                                                 float* __restrict__ ex, float* __restrict__ ey,
+                                                 int H, int W, int x0, int y0, int th,
+                                                 float kappa, float inv_kappa, float cs,
+                                                 unsigned char* smem)
 {
     constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
     const int gr = th + 2 * R;
     float* sf = reinterpret_cast<float*>(smem);
-    float2* gx = reinterpret_cast<float2*>(smem + f_bytes(R, th));
-    float2* gy = gx + gr * gp;
+    float2* g = reinterpret_cast<float2*>(smem + f_bytes(R, th));   // (g_x', g_y') per position
     load_f_tile(f, H, W, x0, y0, R, th, sf);
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        const float vx = grad_x(sf, fp, r, c, kappa), vy = grad_y(sf, fp, r, c, kappa);
-        gx[i] = make_float2(vx, vx);
-        gy[i] = make_float2(vy, vy);
+        g[i] = make_float2(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
     }
     __syncthreads();
 
     const int cx = threadIdx.x & (kTW - 1);
     const int r0 = (threadIdx.x / kTW) * kStrip;
-    float sxs[kStrip], sys[kStrip];
+    u64 S[kStrip], A[kStrip], Z[kStrip];
+    const u64* own = reinterpret_cast<const u64*>(g + (R + r0) * gp + R + cx);
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
-        sxs[j] = gx[(R + r0 + j) * gp + R + cx].x;
-        sys[j] = gy[(R + r0 + j) * gp + R + cx].x;
+        S[j] = own[j * gp];
+        A[j] = Z[j] = 0ull;
     }
-    u64 SX[kPairs], SY[kPairs], AX[kPairs], AY[kPairs], ZX[kPairs], ZY[kPairs];
+    // NA[d] = (n, n), n = (d - R)^2 cs: the dy part of the spatial log2-weight of both lanes
+    u64 NA[2 * R + 1];
 #pragma unroll
-    for (int p = 0; p < kPairs; ++p) {
-        SX[p] = pk(sxs[2 * p], sxs[2 * p + 1]);
-        SY[p] = pk(sys[2 * p], sys[2 * p + 1]);
-        AX[p] = AY[p] = ZX[p] = ZY[p] = 0ull;
-    }
-    // NA[k] = (n(k), n(k-1)) with n(d) = (d-R)^2 cs for d in [0, 2R], kBig outside the window
-    u64 NA[2 * R + 2];
-#pragma unroll
-    for (int k = 0; k <= 2 * R + 1; ++k) {
-        const float lo = (k <= 2 * R) ? float((k - R) * (k - R)) * cs : kBig;
-        const float hi = (k >= 1) ? float((k - 1 - R) * (k - 1 - R)) * cs : kBig;
-        NA[k] = pk(lo, hi);
-        asm volatile("" : "+l"(NA[k]));   // keep the table in registers (no per-use recompute)
+    for (int d = 0; d <= 2 * R; ++d) {
+        const float n = float((d - R) * (d - R)) * cs;
+        NA[d] = pk(n, n);
+        asm volatile("" : "+l"(NA[d]));   // keep the table in registers (no per-use recompute)
     }
 
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
-        const float gdx = ex2_approx(-float(dx * dx) * cs);
+        const float gdx = ex2_approx(-float(dx * dx) * cs);     // the dx part of the weight
         const u64 GD = pk(gdx, gdx);
-        const u64* colx = reinterpret_cast<const u64*>(gx + r0 * gp + R + cx + dx);
-        const u64* coly = reinterpret_cast<const u64*>(gy + r0 * gp + R + cx + dx);
+        const u64* col = reinterpret_cast<const u64*>(g + r0 * gp + R + cx + dx);
 #pragma unroll
         for (int i = 0; i < kStrip + 2 * R; ++i) {
-            const u64 TX = colx[i * gp], TY = coly[i * gp];
-            const u64 TGX = mul2(TX, GD), TGY = mul2(TY, GD);
+            const u64 T = col[i * gp];
+            const u64 TG = mul2(T, GD);
 #pragma unroll
-            for (int p = 0; p < kPairs; ++p) {
-                const int k = i - 2 * p;
-                if (k < 0 || k > 2 * R + 1) continue;
-                float a0, a1, b0, b1;
+            for (int j = 0; j < kStrip; ++j) {
+                const int d = i - j;  // dy + R
+                if (d < 0 || d > 2 * R) continue;
+                float e0, e1;
                 if (RANGE) {
-                    const u64 QX = sub2(TX, SX[p]), QY = sub2(TY, SY[p]);
-                    upk(fma2(QX, QX, NA[k]), a0, a1);
-                    upk(fma2(QY, QY, NA[k]), b0, b1);
+                    const u64 Q = sub2(T, S[j]);
+                    upk(fma2(Q, Q, NA[d]), e0, e1);
                 } else {
-                    upk(NA[k], a0, a1);
-                    b0 = a0;
-                    b1 = a1;
+                    upk(NA[d], e0, e1);
                 }
-                const u64 WX = pk(ex2_approx(-a0), ex2_approx(-a1));
-                const u64 WY = pk(ex2_approx(-b0), ex2_approx(-b1));
-                AX[p] = fma2(WX, TGX, AX[p]);
-                ZX[p] = fma2(WX, GD, ZX[p]);
-                AY[p] = fma2(WY, TGY, AY[p]);
-                ZY[p] = fma2(WY, GD, ZY[p]);
+                u64 Wt;
+                if (BF16W) Wt = bf2_to_f2(ex2_bf2(__floats2bfloat162_rn(-e0, -e1)));
+                else Wt = pk(ex2_approx(-e0), ex2_approx(-e1));
+                A[j] = fma2(Wt, TG, A[j]);
+                Z[j] = fma2(Wt, GD, Z[j]);
             }
         }
     }
-    float ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+    float ax[kStrip], zx[kStrip], sx[kStrip], ay[kStrip], zy[kStrip], sy[kStrip];
 #pragma unroll
-    for (int p = 0; p < kPairs; ++p) {
-        upk(AX[p], ax[2 * p], ax[2 * p + 1]);
-        upk(ZX[p], zx[2 * p], zx[2 * p + 1]);
-        upk(AY[p], ay[2 * p], ay[2 * p + 1]);
-        upk(ZY[p], zy[2 * p], zy[2 * p + 1]);
+    for (int j = 0; j < kStrip; ++j) {
+        upk(A[j], ax[j], ay[j]);
+        upk(Z[j], zx[j], zy[j]);
+        upk(S[j], sx[j], sy[j]);
     }
-    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
-                sxs, ay, zy, sys, inv_kappa);
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sx, ay, zy, sy, inv_kappa);
+}
+
+template <int R, bool RANGE>
+__device__ __forceinline__ void tile_f32(const float* __restrict__ f, float* __restrict__ ex,
+                                         float* __restrict__ ey, int H, int W, int x0, int y0,
+                                         int th, float kappa, float inv_kappa, float cs,
+                                         unsigned char* smem)
+{
+    tile_pair_fields<R, RANGE, false>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+}
+
+template <int R, bool RANGE>
+__device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __restrict__ ex,
+                                          float* __restrict__ ey, int H, int W, int x0, int y0,
+                                          int th, float kappa, float inv_kappa, float cs,
+                                          unsigned char* smem)
+{
+    tile_pair_fields<R, RANGE, true>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -335,106 +347,6 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __r
             zy[2 * p] = fmaf(gdx, qy.x, zy[2 * p]);
             zy[2 * p + 1] = fmaf(gdx, qy.y, zy[2 * p + 1]);
         }
-    }
-    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
-                sxs, ay, zy, sys, inv_kappa);
-}
-
-// ---------------------------------------------------------------------------------------------
-// BF16 weights: exponent in packed FP32, weights by ex2.approx.ftz.bf16x2, widened back to FP32
-// (exact) for the products and sums, which stay in packed FP32.  Same tiles as the FP32 form.
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ u64 bf2_to_f2(__nv_bfloat162 w)
-{
-    const unsigned b = *reinterpret_cast<unsigned*>(&w);
-    return pk(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
-}
-
-template <int R, bool RANGE>
-__device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __restrict__ ex,
-                                          float* __restrict__ ey, int H, int W, int x0,
-                                          int y0, int th, float kappa, float inv_kappa,
-                                          float cs, unsigned char* smem)
-{
-    constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
-    const int gr = th + 2 * R;
-    float* sf = reinterpret_cast<float*>(smem);
-    float2* gx = reinterpret_cast<float2*>(smem + f_bytes(R, th));
-    float2* gy = gx + gr * gp;
-    load_f_tile(f, H, W, x0, y0, R, th, sf);
-    __syncthreads();
-    for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
-        const int r = i / gp, c = i - r * gp;
-        const float vx = grad_x(sf, fp, r, c, kappa), vy = grad_y(sf, fp, r, c, kappa);
-        gx[i] = make_float2(vx, vx);
-        gy[i] = make_float2(vy, vy);
-    }
-    __syncthreads();
-
-    const int cx = threadIdx.x & (kTW - 1);
-    const int r0 = (threadIdx.x / kTW) * kStrip;
-    float sxs[kStrip], sys[kStrip];
-#pragma unroll
-    for (int j = 0; j < kStrip; ++j) {
-        sxs[j] = gx[(R + r0 + j) * gp + R + cx].x;
-        sys[j] = gy[(R + r0 + j) * gp + R + cx].x;
-    }
-    u64 SX[kPairs], SY[kPairs], AX[kPairs], AY[kPairs], ZX[kPairs], ZY[kPairs];
-#pragma unroll
-    for (int p = 0; p < kPairs; ++p) {
-        SX[p] = pk(sxs[2 * p], sxs[2 * p + 1]);
-        SY[p] = pk(sys[2 * p], sys[2 * p + 1]);
-        AX[p] = AY[p] = ZX[p] = ZY[p] = 0ull;
-    }
-    u64 NA[2 * R + 2];
-#pragma unroll
-    for (int k = 0; k <= 2 * R + 1; ++k) {
-        const float lo = (k <= 2 * R) ? float((k - R) * (k - R)) * cs : kBig;
-        const float hi = (k >= 1) ? float((k - 1 - R) * (k - 1 - R)) * cs : kBig;
-        NA[k] = pk(lo, hi);
-        asm volatile("" : "+l"(NA[k]));
-    }
-
-#pragma unroll 1
-    for (int dx = -R; dx <= R; ++dx) {
-        const float gdx = ex2_approx(-float(dx * dx) * cs);
-        const u64 GD = pk(gdx, gdx);
-        const u64* colx = reinterpret_cast<const u64*>(gx + r0 * gp + R + cx + dx);
-        const u64* coly = reinterpret_cast<const u64*>(gy + r0 * gp + R + cx + dx);
-#pragma unroll
-        for (int i = 0; i < kStrip + 2 * R; ++i) {
-            const u64 TX = colx[i * gp], TY = coly[i * gp];
-            const u64 TGX = mul2(TX, GD), TGY = mul2(TY, GD);
-#pragma unroll
-            for (int p = 0; p < kPairs; ++p) {
-                const int k = i - 2 * p;
-                if (k < 0 || k > 2 * R + 1) continue;
-                float a0, a1, b0, b1;
-                if (RANGE) {
-                    const u64 QX = sub2(TX, SX[p]), QY = sub2(TY, SY[p]);
-                    upk(fma2(QX, QX, NA[k]), a0, a1);
-                    upk(fma2(QY, QY, NA[k]), b0, b1);
-                } else {
-                    upk(NA[k], a0, a1);
-                    b0 = a0;
-                    b1 = a1;
-                }
-                const u64 WX = bf2_to_f2(ex2_bf2(__floats2bfloat162_rn(-a0, -a1)));
-                const u64 WY = bf2_to_f2(ex2_bf2(__floats2bfloat162_rn(-b0, -b1)));
-                AX[p] = fma2(WX, TGX, AX[p]);
-                ZX[p] = fma2(WX, GD, ZX[p]);
-                AY[p] = fma2(WY, TGY, AY[p]);
-                ZY[p] = fma2(WY, GD, ZY[p]);
-            }
-        }
-    }
-    float ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
-#pragma unroll
-    for (int p = 0; p < kPairs; ++p) {
-        upk(AX[p], ax[2 * p], ax[2 * p + 1]);
-        upk(ZX[p], zx[2 * p], zx[2 * p + 1]);
-        upk(AY[p], ay[2 * p], ay[2 * p + 1]);
-        upk(ZY[p], zy[2 * p], zy[2 * p + 1]);
     }
     store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
                 sxs, ay, zy, sys, inv_kappa);

@@ -5,7 +5,7 @@
 // every routine starts by assuming its input is visible to all threads (the caller synchronised)
 // and ends with a __syncthreads().
 //
-// Direct transforms (length L = product of the plan's radices):
+// Direct transforms (length L = product of the plan's radices 16, 8, 4, 2, 3, 5, 7):
 //   forward: decimation in frequency, natural input -> output in digit-reversed order
 //            (frequency k at position perm[k]);
 //   inverse: the conjugate stages in reverse order, digit-reversed input -> natural output,
@@ -54,6 +54,40 @@ __device__ __forceinline__ constexpr float root_sin(int R, int k)
                    : k == 2 ? 0.974927912181823607f : 0.433883739117558120f);
 }
 
+// cos(2 pi k / 16), k = 0..4 (mathematical constants)
+__device__ __forceinline__ constexpr float c16(int k)
+{
+    return k == 0 ? 1.0f : k == 1 ? 0.923879532511286756f : k == 2 ? 0.707106781186547524f
+         : k == 3 ? 0.382683432365089772f : 0.0f;
+}
+// w16^e = exp(-+2 pi i e / 16) for e = 0..15 as (cos, sin) with the sign of the transform
+template <bool INV>
+__device__ __forceinline__ float2 w16(int e)
+{
+    e &= 15;
+    const int q = e & 3, quad = e >> 2;      // e = 4 quad + q
+    // exp(-2 pi i e/16) = (-i)^quad * (cos(2 pi q/16) - i sin(2 pi q/16))
+    float cr = c16(q), ci = -c16(4 - q);
+    for (int t = 0; t < quad; ++t) {          // multiply by -i: (a, b) -> (b, -a)
+        const float a = cr;
+        cr = ci;
+        ci = -a;
+    }
+    return INV ? make_float2(cr, -ci) : make_float2(cr, ci);
+}
+
+// In-register 4-point DFT on v[o], v[o+st], v[o+2st], v[o+3st].
+template <bool INV, int N>
+__device__ __forceinline__ void dft4_at(float2 (&v)[N], int o, int st)
+{
+    const float2 a = cadd(v[o], v[o + 2 * st]), b = csub(v[o], v[o + 2 * st]);
+    const float2 c = cadd(v[o + st], v[o + 3 * st]), d = rot_i<INV>(csub(v[o + st], v[o + 3 * st]));
+    v[o] = cadd(a, c);
+    v[o + 2 * st] = csub(a, c);
+    v[o + st] = cadd(b, d);
+    v[o + 3 * st] = csub(b, d);
+}
+
 // In-register R-point DFT, y_q = sum_t x_t w^(t q), w = exp(-+2 pi i / R).
 template <int R, bool INV>
 __device__ __forceinline__ void small_dft(float2 (&v)[R])
@@ -63,12 +97,41 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R])
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     } else if constexpr (R == 4) {
-        const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-        const float2 c = cadd(v[1], v[3]), d = rot_i<INV>(csub(v[1], v[3]));
-        v[0] = cadd(a, c);
-        v[2] = csub(a, c);
-        v[1] = cadd(b, d);
-        v[3] = csub(b, d);
+        dft4_at<INV>(v, 0, 1);
+    } else if constexpr (R == 8) {
+        // 8 = 4 x 2: t = 2 t1 + t2; DFT4 over t1 (stride 2) for each t2, twiddle w8^(t2 k1),
+        // DFT2 over t2; y[k1 + 4 k2] lands at v[2 k1 + k2] before the final reorder.
+        dft4_at<INV>(v, 0, 2);
+        dft4_at<INV>(v, 1, 2);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) v[2 * k1 + 1] = cmul(v[2 * k1 + 1], w16<INV>(2 * k1));
+        float2 y[8];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            y[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
+            y[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = y[k];
+    } else if constexpr (R == 16) {
+        // 16 = 4 x 4: t = 4 t1 + t2; DFT4 over t1 (stride 4) for each t2, twiddle
+        // w16^(t2 k1), DFT4 over t2; y[k1 + 4 k2] lands at v[4 k1 + k2] before the reorder.
+#pragma unroll
+        for (int t2 = 0; t2 < 4; ++t2) dft4_at<INV>(v, t2, 4);
+        // after the first pass v[4 k1 + t2] holds sub-DFT output k1 of column t2
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+            for (int t2 = 1; t2 < 4; ++t2) v[4 * k1 + t2] = cmul(v[4 * k1 + t2], w16<INV>(k1 * t2));
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4_at<INV>(v, 4 * k1, 1);
+        float2 y[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = y[k];
     } else {
         // odd R: pair t with R-t; y_q = x0 + sum_t [(x_t + x_{R-t}) cos -/+ i (x_t - x_{R-t}) sin]
         constexpr int h = (R - 1) / 2;
@@ -103,56 +166,61 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R])
     }
 }
 
-// One decimation-in-frequency stage over blocks of length Lblk = R*m:
-//   inputs x[base + t m], base = blk*Lblk + j;  R-point DFT;  output q times w_Lblk^(j q).
+// One decimation-in-frequency stage over blocks of length R*m:
+//   inputs x[base + t m], base = blk*(R m) + j;  R-point DFT;  output q times w_(R m)^(j q).
+// blk = b / m comes from a multiply-high by the plan's magic number (no integer division).
 template <int R>
-__device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc, int Lw, int Lblk,
-                                          int tw_step, const float2* __restrict__ tw)
+__device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc, int Lw, int m,
+                                          unsigned magic, int tw_step,
+                                          const float2* __restrict__ tw)
 {
-    const int ncols = 1 << lgc;
-    const int m = Lblk / R;
-    const int total = (Lw / R) << lgc;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int col = b & (ncols - 1);
-        const int bi = b >> lgc;
-        const int blk = bi / m;
-        const int j = bi - blk * m;
-        const int base = blk * Lblk + j;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(Lw / R) << lgc;
+    const unsigned um = (unsigned)m, lblk = um * R;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> lgc;
+        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
+        const unsigned j = bi - blk * um;
+        const unsigned base = blk * lblk + j;
         float2 v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = x[((base + t * m) << lgc) + col];
+        for (int t = 0; t < R; ++t) v[t] = x[((base + t * um) << lgc) + col];
         small_dft<R, false>(v);
+        const unsigned jt = j * (unsigned)tw_step;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const float2 w = q ? tw[j * q * tw_step] : make_float2(1.f, 0.f);
-            x[((base + q * m) << lgc) + col] = q ? cmul(v[q], w) : v[q];
+            const float2 w = q ? tw[q * jt] : make_float2(1.f, 0.f);
+            x[((base + q * um) << lgc) + col] = q ? cmul(v[q], w) : v[q];
         }
     }
 }
 
-// The inverse of dif_stage (up to the factor R): inputs times conj(w_Lblk^(j q)), inverse DFT.
+// The inverse of dif_stage (up to the factor R): inputs times conj(w_(R m)^(j q)), inverse DFT.
 template <int R>
-__device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc, int Lw, int Lblk,
-                                              int tw_step, const float2* __restrict__ tw)
+__device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc, int Lw, int m,
+                                              unsigned magic, int tw_step,
+                                              const float2* __restrict__ tw)
 {
-    const int ncols = 1 << lgc;
-    const int m = Lblk / R;
-    const int total = (Lw / R) << lgc;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int col = b & (ncols - 1);
-        const int bi = b >> lgc;
-        const int blk = bi / m;
-        const int j = bi - blk * m;
-        const int base = blk * Lblk + j;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(Lw / R) << lgc;
+    const unsigned um = (unsigned)m, lblk = um * R;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> lgc;
+        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
+        const unsigned j = bi - blk * um;
+        const unsigned base = blk * lblk + j;
+        const unsigned jt = j * (unsigned)tw_step;
         float2 v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const float2 a = x[((base + q * m) << lgc) + col];
-            v[q] = q ? cmulc(a, tw[j * q * tw_step]) : a;
+            const float2 a = x[((base + q * um) << lgc) + col];
+            v[q] = q ? cmulc(a, tw[q * jt]) : a;
         }
         small_dft<R, true>(v);
 #pragma unroll
-        for (int t = 0; t < R; ++t) x[((base + t * m) << lgc) + col] = v[t];
+        for (int t = 0; t < R; ++t) x[((base + t * um) << lgc) + col] = v[t];
     }
 }
 
@@ -160,19 +228,20 @@ __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlan
                                                const float2* tw)
 {
     const int Lw = p.L;
-    int Lblk = Lw;
     for (int s = 0; s < p.nst; ++s) {
-        const int R = p.radix[s];
-        const int tw_step = Lw / Lblk;
+        const int R = p.radix[s], m = p.span[s];
+        const unsigned mg = p.magic[s];
+        const int tw_step = Lw / (m * R);
         switch (R) {
-            case 4: dif_stage<4>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 2: dif_stage<2>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 3: dif_stage<3>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 5: dif_stage<5>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            default: dif_stage<7>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 16: dif_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 8: dif_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 4: dif_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 2: dif_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 3: dif_stage<3>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 5: dif_stage<5>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            default: dif_stage<7>(x, lgc, Lw, m, mg, tw_step, tw); break;
         }
         __syncthreads();
-        Lblk /= R;
     }
 }
 
@@ -180,17 +249,18 @@ __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlan
                                                const float2* tw)
 {
     const int Lw = p.L;
-    int Lblk = 1;
     for (int s = p.nst - 1; s >= 0; --s) {
-        const int R = p.radix[s];
-        Lblk *= R;
-        const int tw_step = Lw / Lblk;
+        const int R = p.radix[s], m = p.span[s];
+        const unsigned mg = p.magic[s];
+        const int tw_step = Lw / (m * R);
         switch (R) {
-            case 4: dit_inv_stage<4>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 2: dit_inv_stage<2>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 3: dit_inv_stage<3>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            case 5: dit_inv_stage<5>(x, lgc, Lw, Lblk, tw_step, tw); break;
-            default: dit_inv_stage<7>(x, lgc, Lw, Lblk, tw_step, tw); break;
+            case 16: dit_inv_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 8: dit_inv_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 4: dit_inv_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 2: dit_inv_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 3: dit_inv_stage<3>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 5: dit_inv_stage<5>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            default: dit_inv_stage<7>(x, lgc, Lw, m, mg, tw_step, tw); break;
         }
         __syncthreads();
     }

@@ -62,12 +62,32 @@ bool factor_direct(int N, std::vector<int>& radices)
     radices.clear();
     if (N < 1) return false;
     int n = N;
-    while (n % 4 == 0) { radices.push_back(4); n /= 4; }
+    while (n % 16 == 0) { radices.push_back(16); n /= 16; }
+    if (n % 8 == 0) { radices.push_back(8); n /= 8; }
+    if (n % 4 == 0) { radices.push_back(4); n /= 4; }
     if (n % 2 == 0) { radices.push_back(2); n /= 2; }
     while (n % 3 == 0) { radices.push_back(3); n /= 3; }
     while (n % 5 == 0) { radices.push_back(5); n /= 5; }
     while (n % 7 == 0) { radices.push_back(7); n /= 7; }
     return n == 1 && int(radices.size()) <= kMaxStages;
+}
+
+bool fill_stage_division(FftPlanDev& d)
+{
+    int span = d.L;
+    for (int s = 0; s < d.nst; ++s) {
+        span /= d.radix[s];
+        d.span[s] = span;
+        d.magic[s] = span == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + span - 1) / span);
+        if (span > 1) {
+            // butterfly indices of one column reach L / radix[s]: check every quotient
+            const unsigned nb = (unsigned)(d.L / d.radix[s]);
+            for (unsigned b = 0; b < nb; ++b)
+                if ((unsigned)(((unsigned long long)b * d.magic[s]) >> 32) != b / (unsigned)span)
+                    return false;
+        }
+    }
+    return true;
 }
 
 cudaError_t build_fft_plan(int N, FftPlanHost& out)
@@ -88,6 +108,7 @@ cudaError_t build_fft_plan(int N, FftPlanHost& out)
     d.bluestein = direct ? 0 : 1;
     d.nst = int(radices.size());
     for (int s = 0; s < d.nst; ++s) d.radix[s] = radices[s];
+    if (!fill_stage_division(d)) return cudaErrorInvalidValue;
 
     // Host tables.
     std::vector<float2> tw(L);
@@ -195,6 +216,7 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     rel.bluestein = direct ? 0 : 1;
     rel.nst = int(radices.size());
     for (int s = 0; s < rel.nst; ++s) rel.radix[s] = radices[s];
+    if (!fill_stage_division(rel)) return false;
 
     std::vector<float2> tw(L);
     for (int m = 0; m < L; ++m) {

@@ -11,7 +11,7 @@ namespace blfls {
 
 // ---------------------------------------------------------------------------------------------
 // FFT plans.  A transform of length N is either a direct in-place mixed-radix FFT (N factors
-// into 2, 3, 4, 5, 7) or Bluestein's chirp-z algorithm over a direct power-of-two FFT of length
+// into 16, 8, 4, 2, 3, 5, 7) or Bluestein's chirp-z algorithm over a direct power-of-two FFT of length
 // L >= 2N - 1.  The direct forward transform is decimation in frequency: natural-order input,
 // output in mixed-radix digit-reversed order, so frequency k sits at position perm[k].  The
 // inverse runs the conjugate stages in reverse order and takes that order back to natural.
@@ -27,6 +27,8 @@ struct FftPlanDev {
     int nst;        // number of direct stages
     int bluestein;  // 0 / 1
     int radix[kMaxStages];
+    int span[kMaxStages];            // m_s = L / (radix[0] ... radix[s]): butterfly span of stage s
+    unsigned magic[kMaxStages];      // ceil(2^32 / m_s): b / m_s = umulhi(b, magic) (0 when m_s = 1)
     const float2* tw;      // L entries: exp(-2 pi i m / L)
     const int* perm;       // N entries: work position of frequency k (identity for Bluestein)
     const int* iperm;      // L entries: frequency held at work position p (direct only)
@@ -44,6 +46,8 @@ struct FftPlanHost {
 
 // Factor N for the direct path; returns false when N has a prime factor above 7.
 bool factor_direct(int N, std::vector<int>& radices);
+// Fill span[] and magic[] from radix[] (and check the magic divisions exhaustively).
+bool fill_stage_division(FftPlanDev& d);
 // Build the host tables of a plan and upload them (cudaMalloc'd, owned by the caller).
 cudaError_t build_fft_plan(int N, FftPlanHost& out);
 void free_fft_plan(FftPlanHost& p);

@@ -16,11 +16,13 @@
 // K4 (rows, inverse): rebuilds the full row spectrum of two rows from their halves (Hermitian
 //    symmetry), inverse FFT, and writes u = f + result (real part row a, imaginary part row b).
 //
-// Each phase is written once as a per-item device function (a row pair, or a block of columns)
-// and driven either by a single-image persistent grid (twiddles staged in shared memory once per
-// CTA) or by a batched persistent grid over the items of many jobs (twiddles read through L1,
-// since consecutive items may belong to different transform lengths).  Both drivers run the
-// same arithmetic, so a job's result does not depend on the batch it ran in.
+// Each phase is written once as a per-item compute function (a row pair, or a block of columns)
+// and driven by one of three persistent grids: the staged single-image drivers (each CTA walks a
+// contiguous band of items and copies the next item into shared memory with cp.async while it
+// transforms the current one, double-buffered); the plain single-image drivers (loads then
+// transform, twiddles staged in shared memory once per CTA), used when the staged buffers do not
+// fit; and the batched drivers over the items of many jobs.  All run the same arithmetic, so a
+// job's result does not depend on the driver or the batch it ran in.
 #include "fft_device.cuh"
 
 namespace blfls {
@@ -39,32 +41,24 @@ __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const F
     return tw_smem;
 }
 
-// K2: row pair `pair` (rows 2 pair, 2 pair + 1) of one channel.
-__device__ __forceinline__ void k2_item(const float* __restrict__ ex, const float* __restrict__ ey,
-                                        float2* __restrict__ spec, int H, int W, int pair,
-                                        const FftPlanDev& rp, const float2* tw, float2* data)
+// K2 on one row pair, given its rows (in global or shared memory): r = D_x^T e_x + D_y^T e_y for
+// rows y0 and y1 packed as z = r0 + i r1, forward FFT, split into the two half spectra s0, s1.
+__device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, const float* eym,
+                                        const float* ey0, const float* ey1, bool has1, int W,
+                                        float2* s0, float2* s1, const FftPlanDev& rp,
+                                        const float2* tw, float2* data)
 {
     const int Wh = W / 2 + 1;
-    const int y0 = 2 * pair, y1 = y0 + 1;
-    const bool has1 = y1 < H;
-    const int ym = (y0 == 0) ? H - 1 : y0 - 1;
-    const float* ex0 = ex + (size_t)y0 * W;
-    const float* ey0 = ey + (size_t)y0 * W;
-    const float* eym = ey + (size_t)ym * W;
-    const float* ex1 = ex + (size_t)(has1 ? y1 : y0) * W;
-    const float* ey1 = ey + (size_t)(has1 ? y1 : y0) * W;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int xm = (x == 0) ? W - 1 : x - 1;
         // (D_x^T e_x)[y][x] = e_x[y][x-1] - e_x[y][x];  (D_y^T e_y)[y][x] = e_y[y-1][x] - e_y[y][x]
-        const float r0 = (__ldg(ex0 + xm) - __ldg(ex0 + x)) + (__ldg(eym + x) - __ldg(ey0 + x));
+        const float r0 = (ex0[xm] - ex0[x]) + (eym[x] - ey0[x]);
         float r1 = 0.f;
-        if (has1) r1 = (__ldg(ex1 + xm) - __ldg(ex1 + x)) + (__ldg(ey0 + x) - __ldg(ey1 + x));
+        if (has1) r1 = (ex1[xm] - ex1[x]) + (ey0[x] - ey1[x]);
         data[x] = make_float2(r0, r1);
     }
     __syncthreads();
     fft_forward(data, 0, rp, tw);
-    float2* s0 = spec + (size_t)y0 * Wh;
-    float2* s1 = spec + (size_t)(has1 ? y1 : y0) * Wh;
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
         const float2 zk = data[__ldg(rp.perm + k)];
@@ -74,6 +68,46 @@ __device__ __forceinline__ void k2_item(const float* __restrict__ ex, const floa
         if (has1) s1[k] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
     }
     __syncthreads();
+}
+
+// K2: row pair `pair` (rows 2 pair, 2 pair + 1) of one channel, read from global memory.
+__device__ __forceinline__ void k2_item(const float* __restrict__ ex, const float* __restrict__ ey,
+                                        float2* __restrict__ spec, int H, int W, int pair,
+                                        const FftPlanDev& rp, const float2* tw, float2* data)
+{
+    const int Wh = W / 2 + 1;
+    const int y0 = 2 * pair, y1 = y0 + 1;
+    const bool has1 = y1 < H;
+    const int ym = (y0 == 0) ? H - 1 : y0 - 1;
+    const int yb = has1 ? y1 : y0;
+    k2_rows(ex + (size_t)y0 * W, ex + (size_t)yb * W, ey + (size_t)ym * W, ey + (size_t)y0 * W,
+            ey + (size_t)yb * W, has1, W, spec + (size_t)y0 * Wh, spec + (size_t)yb * Wh, rp, tw,
+            data);
+}
+
+// K3 on one column block already in `data` (rows n < H; the caller synchronised): forward FFT
+// down the columns, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the 1/(HW) of the
+// inverse), inverse FFT.  Ends synchronised.
+__device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int kx0, int lgc,
+                                               const FftPlanDev& cp, const float* __restrict__ sx,
+                                               const float* __restrict__ sy, float lam,
+                                               float scale, const float2* tw)
+{
+    const int CB = 1 << lgc;
+    const int Wh = W / 2 + 1;
+    fft_forward(data, lgc, cp, tw);
+    const int nfreq = cp.bluestein ? H : cp.L;
+    for (int i = threadIdx.x; i < (nfreq << lgc); i += blockDim.x) {
+        const int p = i >> lgc, c = i & (CB - 1);
+        const int kx = min(kx0 + c, Wh - 1);
+        const int ky = __ldg(cp.iperm + p);
+        const float den = fmaf(lam, __ldg(sx + kx) + __ldg(sy + ky), 1.0f);
+        const float m = __fdividef(scale, den) * lam;
+        const float2 v = data[i];
+        data[i] = make_float2(v.x * m, v.y * m);
+    }
+    __syncthreads();
+    fft_inverse(data, lgc, cp, tw);
 }
 
 // K3: columns [blk * 2^lgc, (blk + 1) * 2^lgc) of the half spectrum of one channel.
@@ -91,20 +125,7 @@ __device__ __forceinline__ void k3_item(float2* __restrict__ spec, int H, int W,
         data[i] = (kx < Wh) ? spec[(size_t)n * Wh + kx] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_forward(data, lgc, cp, tw);
-    // spectral divide (Eq. 8 denominator, F(1) = 1), with lam and the 1/(HW) of the inverse
-    const int nfreq = cp.bluestein ? H : cp.L;
-    for (int i = threadIdx.x; i < (nfreq << lgc); i += blockDim.x) {
-        const int p = i >> lgc, c = i & (CB - 1);
-        const int kx = min(kx0 + c, Wh - 1);
-        const int ky = __ldg(cp.iperm + p);
-        const float den = fmaf(lam, __ldg(sx + kx) + __ldg(sy + ky), 1.0f);
-        const float m = __fdividef(scale, den) * lam;
-        const float2 v = data[i];
-        data[i] = make_float2(v.x * m, v.y * m);
-    }
-    __syncthreads();
-    fft_inverse(data, lgc, cp, tw);
+    k3_solve_block(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tw);
     for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
         const int n = i >> lgc, c = i & (CB - 1);
         const int kx = kx0 + c;
@@ -113,16 +134,13 @@ __device__ __forceinline__ void k3_item(float2* __restrict__ spec, int H, int W,
     __syncthreads();
 }
 
-// K4: row pair `pair` of one channel: u = f + inverse row FFT of the corrected spectrum.
-__device__ __forceinline__ void k4_item(const float2* __restrict__ spec, const float* f, float* out,
-                                        int H, int W, int pair, const FftPlanDev& rp,
-                                        const float2* tw, float2* data)
+// K4 on one row pair, given its half spectra and input rows (global or shared memory):
+// rebuild Z = A + i B over all W bins, inverse FFT, u = f + result.
+__device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool has1,
+                                        const float* f0, const float* f1, float* o0, float* o1,
+                                        int W, const FftPlanDev& rp, const float2* tw,
+                                        float2* data)
 {
-    const int Wh = W / 2 + 1;
-    const int y0 = 2 * pair, y1 = y0 + 1;
-    const bool has1 = y1 < H;
-    const float2* s0 = spec + (size_t)y0 * Wh;
-    const float2* s1 = spec + (size_t)(has1 ? y1 : y0) * Wh;
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
         const bool upper = k > W / 2;
         const int kk = upper ? W - k : k;
@@ -135,14 +153,74 @@ __device__ __forceinline__ void k4_item(const float2* __restrict__ spec, const f
     }
     __syncthreads();
     fft_inverse(data, 0, rp, tw);
-    const float* f0 = f + (size_t)y0 * W;
-    float* o0 = out + (size_t)y0 * W;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const float2 z = data[x];
         o0[x] = f0[x] + z.x;
-        if (has1) out[(size_t)y1 * W + x] = f[(size_t)y1 * W + x] + z.y;
+        if (has1) o1[x] = f1[x] + z.y;
     }
     __syncthreads();
+}
+
+// K4: row pair `pair` of one channel, read from global memory.
+__device__ __forceinline__ void k4_item(const float2* __restrict__ spec, const float* f, float* out,
+                                        int H, int W, int pair, const FftPlanDev& rp,
+                                        const float2* tw, float2* data)
+{
+    const int Wh = W / 2 + 1;
+    const int y0 = 2 * pair, y1 = y0 + 1;
+    const bool has1 = y1 < H;
+    const int yb = has1 ? y1 : y0;
+    k4_rows(spec + (size_t)y0 * Wh, spec + (size_t)yb * Wh, has1, f + (size_t)y0 * W,
+            f + (size_t)yb * W, out + (size_t)y0 * W, out + (size_t)yb * W, W, rp, tw, data);
+}
+
+// ---- asynchronous staging (cp.async) --------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async4(void* s, const void* g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* s, const void* g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage n floats (a row) into shared memory: 16-byte copies when src and dst are 16-byte aligned
+// and n % 4 == 0 (`vec`), else 4-byte copies.
+__device__ __forceinline__ void stage_floats(float* dst, const float* src, int n, bool vec)
+{
+    if (vec) {
+        for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(dst + i, src + i);
+    }
+}
+__device__ __forceinline__ void stage_complex(float2* dst, const float2* src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async8(dst + i, src + i);
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Contiguous band of items [b0, b1) of a CTA when n items are split over gridDim.x CTAs.
+__device__ __forceinline__ void band(int n, int& b0, int& b1)
+{
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    b0 = min(n, blockIdx.x * per);
+    b1 = min(n, b0 + per);
 }
 
 // ---- single image --------------------------------------------------------------------------
@@ -177,6 +255,171 @@ __global__ void __launch_bounds__(512) k4_rows_inverse(
     const int npairs = (H + 1) / 2;
     for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x)
         k4_item(spec, f, out, H, W, pair, rp, tw, smem);
+}
+
+// ---- single image, staged: each CTA walks a contiguous band of items and copies the next item
+// into shared memory with cp.async while the current one is transformed. -----------------------
+
+// Shared-memory layouts (bytes).
+__host__ __device__ __forceinline__ size_t k2s_stage_bytes(int W) { return align16(sizeof(float) * 4 * (size_t)W); }
+__host__ __device__ __forceinline__ size_t k2s_smem(int W, int L)
+{
+    return 2 * k2s_stage_bytes(W) + align16(sizeof(float) * (size_t)W) + sizeof(float2) * (size_t)L;
+}
+__host__ __device__ __forceinline__ size_t k4s_stage_bytes(int W)
+{
+    return align16(sizeof(float2) * 2 * (size_t)(W / 2 + 1)) + align16(sizeof(float) * 2 * (size_t)W);
+}
+__host__ __device__ __forceinline__ size_t k4s_smem(int W, int L)
+{
+    return 2 * k4s_stage_bytes(W) + sizeof(float2) * (size_t)L;
+}
+__host__ __device__ __forceinline__ size_t k3s_smem(int L, int lgc)
+{
+    return 2 * (sizeof(float2) * (size_t)L << lgc);
+}
+
+__global__ void __launch_bounds__(512) k2_rows_staged(const float* __restrict__ ex,
+                                                      const float* __restrict__ ey,
+                                                      float2* __restrict__ spec, int H, int W,
+                                                      FftPlanDev rp, int vec)
+{
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    unsigned char* smem = staged_smem;
+    float* stage = reinterpret_cast<float*>(smem);                       // [2][4][W]
+    const size_t sb = k2s_stage_bytes(W) / sizeof(float);
+    float* eyprev = reinterpret_cast<float*>(smem + 2 * k2s_stage_bytes(W));
+    float2* data = reinterpret_cast<float2*>(smem + 2 * k2s_stage_bytes(W) + align16(sizeof(float) * W));
+    const int Wh = W / 2 + 1;
+    const int npairs = (H + 1) / 2;
+    int p0, p1;
+    band(npairs, p0, p1);
+    if (p0 >= p1) return;
+    auto issue = [&](int p, float* st) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        stage_floats(st, ex + (size_t)y0 * W, W, vec);
+        stage_floats(st + 2 * W, ey + (size_t)y0 * W, W, vec);
+        if (y1 < H) {
+            stage_floats(st + W, ex + (size_t)y1 * W, W, vec);
+            stage_floats(st + 3 * W, ey + (size_t)y1 * W, W, vec);
+        }
+    };
+    stage_floats(eyprev, ey + (size_t)(p0 == 0 ? H - 1 : 2 * p0 - 1) * W, W, vec);
+    issue(p0, stage);
+    cp_commit();
+    for (int p = p0; p < p1; ++p) {
+        float* st = stage + ((p - p0) & 1) * sb;
+        if (p + 1 < p1) {
+            issue(p + 1, stage + (((p - p0) & 1) ^ 1) * sb);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const bool has1 = y1 < H;
+        // k2_rows' first loop reads eyprev; its first barrier precedes the FFT, so eyprev can be
+        // refreshed (for the next pair) right after it returns.
+        k2_rows(st, st + W, eyprev, st + 2 * W, st + 3 * W, has1, W, spec + (size_t)y0 * Wh,
+                spec + (size_t)(has1 ? y1 : y0) * Wh, rp, rp.tw, data);
+        if (has1)
+            for (int x = threadIdx.x; x < W; x += blockDim.x) eyprev[x] = st[3 * W + x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(512) k4_rows_staged(const float2* __restrict__ spec,
+                                                      const float* f, float* out, int H, int W,
+                                                      FftPlanDev rp, int vec)
+{
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    unsigned char* smem = staged_smem;
+    const int Wh = W / 2 + 1;
+    const size_t sb = k4s_stage_bytes(W);
+    const size_t so = align16(sizeof(float2) * 2 * (size_t)Wh);    // f rows after the spectra
+    float2* data = reinterpret_cast<float2*>(smem + 2 * sb);
+    const int npairs = (H + 1) / 2;
+    int p0, p1;
+    band(npairs, p0, p1);
+    if (p0 >= p1) return;
+    auto issue = [&](int p, unsigned char* st) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        float2* ss = reinterpret_cast<float2*>(st);
+        float* sf = reinterpret_cast<float*>(st + so);
+        stage_complex(ss, spec + (size_t)y0 * Wh, Wh);
+        stage_floats(sf, f + (size_t)y0 * W, W, vec);
+        if (y1 < H) {
+            stage_complex(ss + Wh, spec + (size_t)y1 * Wh, Wh);
+            stage_floats(sf + W, f + (size_t)y1 * W, W, vec);
+        }
+    };
+    issue(p0, smem);
+    cp_commit();
+    for (int p = p0; p < p1; ++p) {
+        unsigned char* st = smem + ((p - p0) & 1) * sb;
+        if (p + 1 < p1) {
+            issue(p + 1, smem + (((p - p0) & 1) ^ 1) * sb);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const bool has1 = y1 < H;
+        const float2* ss = reinterpret_cast<const float2*>(st);
+        const float* sf = reinterpret_cast<const float*>(st + so);
+        k4_rows(ss, ss + Wh, has1, sf, sf + W, out + (size_t)y0 * W,
+                out + (size_t)(has1 ? y1 : y0) * W, W, rp, rp.tw, data);
+    }
+}
+
+__global__ void __launch_bounds__(512) k3_cols_staged(float2* __restrict__ spec, int H, int W,
+                                                      FftPlanDev cp, const float* __restrict__ sx,
+                                                      const float* __restrict__ sy, float lam,
+                                                      float scale, int lgc)
+{
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    unsigned char* smem = staged_smem;
+    const int CB = 1 << lgc;
+    const int Wh = W / 2 + 1;
+    const size_t blk_elems = (size_t)cp.L << lgc;
+    float2* bufs = reinterpret_cast<float2*>(smem);
+    const int nblk = (Wh + CB - 1) >> lgc;
+    int b0, b1;
+    band(nblk, b0, b1);
+    if (b0 >= b1) return;
+    auto issue = [&](int b, float2* buf) {
+        const int kx0 = b * CB;
+        for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
+            const int n = i >> lgc, c = i & (CB - 1);
+            const int kx = kx0 + c;
+            if (kx < Wh) cp_async8(buf + i, spec + (size_t)n * Wh + kx);
+            else buf[i] = make_float2(0.f, 0.f);
+        }
+    };
+    issue(b0, bufs);
+    cp_commit();
+    for (int b = b0; b < b1; ++b) {
+        float2* data = bufs + ((b - b0) & 1) * blk_elems;
+        if (b + 1 < b1) {
+            issue(b + 1, bufs + (((b - b0) & 1) ^ 1) * blk_elems);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const int kx0 = b * CB;
+        k3_solve_block(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, cp.tw);
+        for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
+            const int n = i >> lgc, c = i & (CB - 1);
+            const int kx = kx0 + c;
+            if (kx < Wh) spec[(size_t)n * Wh + kx] = data[i];
+        }
+        __syncthreads();
+    }
 }
 
 // ---- batched: items of many jobs ------------------------------------------------------------
@@ -254,6 +497,9 @@ void init_solve_kernel_attributes()
     cudaFuncSetAttribute(k2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k3_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k2_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k4_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 size_t solve_smem_rows(const FftPlanDev& rp)
@@ -284,31 +530,71 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
                                   cudaStream_t s, int num_sms, const cudaEvent_t* marks)
 {
     const int H = p.H, W = p.W;
-    const int lgc = solve_fit_lgc(cp.L, p.col_block);
-    const int CB = 1 << lgc;
-
-    const size_t smem_r = solve_smem_rows(rp);
-    const int tw_r = smem_r > sizeof(float2) * rp.L;
-    const int thr_r = threads_for(rp.L / 4);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_forward, thr_r, smem_r);
-    const int npairs = (H + 1) / 2;
-    const int grid_r = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
-
-    const size_t smem_c = solve_smem_cols(cp, CB);
-    const int tw_c = smem_c > sizeof(float2) * (size_t)cp.L * CB;
-    const int thr_c = threads_for((cp.L * CB) / 4);
-    int occ_c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k3_cols_solve, thr_c, smem_c);
-    const int nblk = (W / 2 + 1 + CB - 1) / CB;
-    const int grid_c = std::max(1, std::min(nblk, num_sms * std::max(occ_c, 1)));
-
-    k2_rows_forward<<<grid_r, thr_r, smem_r, s>>>(ex, ey, spec, H, W, rp, tw_r);
-    if (marks) cudaEventRecord(marks[0], s);
     const float scale = 1.0f / ((float)H * (float)W);
-    k3_cols_solve<<<grid_c, thr_c, smem_c, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc, tw_c);
+    // Staged drivers when their double-buffered shared memory fits; rows of floats are copied
+    // 16 bytes at a time when every row start is 16-byte aligned.
+    const size_t cap = kSmemCap;
+    const bool al16 = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(ex) | reinterpret_cast<uintptr_t>(ey) |
+                                        reinterpret_cast<uintptr_t>(f)) % 16 == 0);
+    const bool rows_staged = k2s_smem(W, rp.L) <= cap && k4s_smem(W, rp.L) <= cap;
+    int lgc = solve_fit_lgc(cp.L, p.col_block);
+    while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
+    const bool cols_staged = k3s_smem(cp.L, lgc) <= cap;
+    const int CB = 1 << lgc;
+    const int npairs = (H + 1) / 2;
+    const int nblk = (W / 2 + 1 + CB - 1) / CB;
+
+    if (rows_staged) {
+        const size_t sm2 = k2s_smem(W, rp.L);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_staged, 512, sm2);
+        const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
+        k2_rows_staged<<<grid, 512, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
+    } else {
+        const size_t smem_r = solve_smem_rows(rp);
+        const int tw_r = smem_r > sizeof(float2) * rp.L;
+        const int thr_r = threads_for(rp.L / 4);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_forward, thr_r, smem_r);
+        const int grid_r = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
+        k2_rows_forward<<<grid_r, thr_r, smem_r, s>>>(ex, ey, spec, H, W, rp, tw_r);
+    }
+    if (marks) cudaEventRecord(marks[0], s);
+    if (cols_staged) {
+        const size_t sm3 = k3s_smem(cp.L, lgc);
+        const int thr = threads_for((cp.L * CB) / 4);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_cols_staged, thr, sm3);
+        const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
+        k3_cols_staged<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc);
+    } else {
+        const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
+        const int CB1 = 1 << lgc1;
+        const size_t smem_c = solve_smem_cols(cp, CB1);
+        const int tw_c = smem_c > sizeof(float2) * (size_t)cp.L * CB1;
+        const int thr_c = threads_for((cp.L * CB1) / 4);
+        int occ_c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k3_cols_solve, thr_c, smem_c);
+        const int nblk1 = (W / 2 + 1 + CB1 - 1) / CB1;
+        const int grid_c = std::max(1, std::min(nblk1, num_sms * std::max(occ_c, 1)));
+        k3_cols_solve<<<grid_c, thr_c, smem_c, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc1, tw_c);
+    }
     if (marks) cudaEventRecord(marks[1], s);
-    k4_rows_inverse<<<grid_r, thr_r, smem_r, s>>>(spec, f, out, H, W, rp, tw_r);
+    if (rows_staged) {
+        const size_t sm4 = k4s_smem(W, rp.L);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_staged, 512, sm4);
+        const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
+        k4_rows_staged<<<grid, 512, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
+    } else {
+        const size_t smem_r = solve_smem_rows(rp);
+        const int tw_r = smem_r > sizeof(float2) * rp.L;
+        const int thr_r = threads_for(rp.L / 4);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_inverse, thr_r, smem_r);
+        const int grid_r = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
+        k4_rows_inverse<<<grid_r, thr_r, smem_r, s>>>(spec, f, out, H, W, rp, tw_r);
+    }
     return cudaGetLastError();
 }
 
