@@ -63,6 +63,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of x over all ranks of the default process group (x itself when there is
+    none); the tensor lives on `device` (a CUDA device under NCCL, the CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, max_seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas: all units over the slowest rank."""
+    return world * units_per_rank / max_seconds
+
+
 # ------------------------------------------------------------------------------------------
 # nvidia-smi clock sampling during the timed region
 # ------------------------------------------------------------------------------------------
@@ -362,14 +379,10 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
     ms_per_step = total_ms / K
     mp = H * W / 1e6
-    value = world * mp / (ms_per_step / 1e3)
+    value = replica_throughput(mp, ms_per_step / 1e3, world)
 
     # roofline of the dominant kernel (K1): taps per launch / average launch time
     taps_per_launch = H * W * 2 * (2 * p["radius"] + 1) ** 2          # one channel per launch
@@ -378,7 +391,7 @@ def main():
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = ex2_units * n_sm * sm_mhz * 1e6 / 1e9
     total_prof = sum(prof_ms)
-    roofline = {"bound": "alu", "kernel": "k1_blf_tiled<10,range> (bilateral residuals)",
+    roofline = {"bound": "alu", "kernel": "k1_blf<10,range,fp32> (bilateral residuals)",
                 "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Gtap/s",
                 "frac": round(achieved / peak, 4), "traffic": k1_traffic_per_launch(),
                 "peak_basis": f"MUFU ex2.f32: {ex2_units:.0f}/clk/SM (probe measured "
@@ -404,13 +417,9 @@ def main():
         for _ in range(n_e2e):
             blfls.blfls_smooth_host(h, hx, hy, H, W, C, p["lam"], p["sigma_s"], p["sigma_r"],
                                     p["radius"], p["iters"], 0, stream)
-        e2e_s = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, dev)
         nbytes = C * H * W * 4
-        e2e = {"value": round(world * mp / e2e_s, 2), "unit": "MP/s",
+        e2e = {"value": round(replica_throughput(mp, e2e_s, world), 2), "unit": "MP/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "api": "blfls_smooth_host (pinned host buffers)"}
 

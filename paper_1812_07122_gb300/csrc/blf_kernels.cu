@@ -149,9 +149,9 @@ __global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ e
 
 size_t blf_templ_smem_bytes(int R, int prec, int th)
 {
-    // FP16: two half2 tiles (one per field); FP32 / BF16: one tile of (g_x, g_y) float2 pairs
-    if (prec == 1) return tile_smem_bytes(R, sizeof(__half2), th);
-    return f_bytes(R, th) + sizeof(float2) * (size_t)g_rows(R, th) * g_pitch(R);
+    // one tile of (g_x, g_y) pairs: half2 for FP16W, float2 for FP32 and BF16W
+    const size_t pair = (prec == 1) ? sizeof(__half2) : sizeof(float2);
+    return f_bytes(R, th) + pair * (size_t)g_rows(R, th) * g_pitch(R);
 }
 
 int blf_tile_height(int th)

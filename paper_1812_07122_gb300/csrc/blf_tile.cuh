@@ -14,9 +14,10 @@
 // weighted values and sum of weights) -- three instructions per tap.
 //
 // Precision forms (same tiling):
-//   FP16W: tiles, exponent, weights and products in half2 (ex2.approx.f16x2 gives two weights per
-//          MUFU operation); the products and weights of one window column are summed in half2
-//          and flushed into FP32 accumulators (scaled by exp2(a_dx)) after every column.
+//   FP16W: the same field packing in half2 lanes: tile, exponent, weights and products in half2
+//          (ex2.approx.f16x2 gives both fields' weights per MUFU operation); the products and
+//          weights of one window column are summed in half2 and flushed into FP32 accumulators
+//          (scaled by exp2(a_dx)) after every column.
 //   BF16W: as FP32 but the weights are rounded to BF16 by ex2.approx.ftz.bf16x2, then widened
 //          (exactly) to FP32 for the products and sums.
 // Radii up to kMaxTemplR are compiled with the window unrolled per column; larger radii up to
@@ -257,99 +258,90 @@ __device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP16 weights: exponent, weights and products in half2; per-column sums flushed to FP32
+// FP16 weights: the two gradient fields in the two half2 lanes; exponent, weights and products
+// in half2 (ex2.approx.f16x2 gives both fields' weights in one MUFU operation); each window
+// column's sums of w t and w are kept in half2 and flushed into FP32 accumulators (scaled by
+// the column's spatial factor exp2(a_dx)) after every column.
 // ---------------------------------------------------------------------------------------------
 template <int R, bool RANGE>
 __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __restrict__ ex,
-                                          float* __restrict__ ey, int H, int W, int x0,
-                                          int y0, int th, float kappa, float inv_kappa,
-                                          float cs, unsigned char* smem)
+                                         float* __restrict__ ey, int H, int W, int x0,
+                                         int y0, int th, float kappa, float inv_kappa,
+                                         float cs, unsigned char* smem)
 {
     constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
     const int gr = th + 2 * R;
     float* sf = reinterpret_cast<float*>(smem);
-    __half2* gx = reinterpret_cast<__half2*>(smem + f_bytes(R, th));
-    __half2* gy = gx + gr * gp;
+    __half2* g = reinterpret_cast<__half2*>(smem + f_bytes(R, th));   // (g_x', g_y') per position
     load_f_tile(f, H, W, x0, y0, R, th, sf);
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        gx[i] = __float2half2_rn(grad_x(sf, fp, r, c, kappa));
-        gy[i] = __float2half2_rn(grad_y(sf, fp, r, c, kappa));
+        g[i] = __floats2half2_rn(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
     }
     __syncthreads();
 
     const int cx = threadIdx.x & (kTW - 1);
     const int r0 = (threadIdx.x / kTW) * kStrip;
-    float sxs[kStrip], sys[kStrip], ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+    __half2 S[kStrip];
+    u64 A[kStrip], Z[kStrip];
+    float sxs[kStrip], sys[kStrip];
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
+        S[j] = g[(R + r0 + j) * gp + R + cx];
         sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, kappa);   // FP32 centre values
         sys[j] = grad_y(sf, fp, R + r0 + j, R + cx, kappa);
-        ax[j] = zx[j] = ay[j] = zy[j] = 0.f;
+        A[j] = Z[j] = 0ull;
     }
-    __half2 SX[kPairs], SY[kPairs];
+    // AD[d] = (a, a), a = -(d - R)^2 cs: the dy part of the spatial log2-weight of both lanes
+    __half2 AD[2 * R + 1];
 #pragma unroll
-    for (int p = 0; p < kPairs; ++p) {
-        SX[p] = __lows2half2(gx[(R + r0 + 2 * p) * gp + R + cx], gx[(R + r0 + 2 * p + 1) * gp + R + cx]);
-        SY[p] = __lows2half2(gy[(R + r0 + 2 * p) * gp + R + cx], gy[(R + r0 + 2 * p + 1) * gp + R + cx]);
-    }
-    // A[k] = (a(k), a(k-1)), a(d) = -(d-R)^2 cs inside the window, -inf outside
-    __half2 A[2 * R + 2];
-#pragma unroll
-    for (int k = 0; k <= 2 * R + 1; ++k) {
-        const float lo = (k <= 2 * R) ? -float((k - R) * (k - R)) * cs : -INFINITY;
-        const float hi = (k >= 1) ? -float((k - 1 - R) * (k - 1 - R)) * cs : -INFINITY;
-        A[k] = __floats2half2_rn(lo, hi);
-        asm volatile("" : "+r"(*reinterpret_cast<unsigned*>(&A[k])));
+    for (int d = 0; d <= 2 * R; ++d) {
+        AD[d] = __float2half2_rn(-float((d - R) * (d - R)) * cs);
+        asm volatile("" : "+r"(*reinterpret_cast<unsigned*>(&AD[d])));
     }
     const __half2 hz = __float2half2_rn(0.f);
 
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
         const float gdx = ex2_approx(-float(dx * dx) * cs);
-        __half2 PX[kPairs], PY[kPairs], QX[kPairs], QY[kPairs];   // partial sums of w t and w
+        const u64 GD = pk(gdx, gdx);
+        __half2 P[kStrip], Q[kStrip];    // this column's sums of w t and w
 #pragma unroll
-        for (int p = 0; p < kPairs; ++p) PX[p] = PY[p] = QX[p] = QY[p] = hz;
-        const __half2* colx = gx + r0 * gp + R + cx + dx;
-        const __half2* coly = gy + r0 * gp + R + cx + dx;
+        for (int j = 0; j < kStrip; ++j) P[j] = Q[j] = hz;
+        const __half2* col = g + r0 * gp + R + cx + dx;
 #pragma unroll
         for (int i = 0; i < kStrip + 2 * R; ++i) {
-            const __half2 TX = colx[i * gp], TY = coly[i * gp];
+            const __half2 T = col[i * gp];
 #pragma unroll
-            for (int p = 0; p < kPairs; ++p) {
-                const int k = i - 2 * p;
-                if (k < 0 || k > 2 * R + 1) continue;
-                __half2 WX, WY;
+            for (int j = 0; j < kStrip; ++j) {
+                const int d = i - j;  // dy + R
+                if (d < 0 || d > 2 * R) continue;
+                __half2 Wt;
                 if (RANGE) {
-                    const __half2 dX = __hsub2(TX, SX[p]), dY = __hsub2(TY, SY[p]);
-                    WX = ex2_h2(__hfma2(__hneg2(dX), dX, A[k]));
-                    WY = ex2_h2(__hfma2(__hneg2(dY), dY, A[k]));
+                    const __half2 D = __hsub2(T, S[j]);
+                    Wt = ex2_h2(__hfma2(__hneg2(D), D, AD[d]));
                 } else {
-                    WX = WY = ex2_h2(A[k]);
+                    Wt = ex2_h2(AD[d]);
                 }
-                PX[p] = __hfma2(WX, TX, PX[p]);
-                QX[p] = __hadd2(QX[p], WX);
-                PY[p] = __hfma2(WY, TY, PY[p]);
-                QY[p] = __hadd2(QY[p], WY);
+                P[j] = __hfma2(Wt, T, P[j]);
+                Q[j] = __hadd2(Q[j], Wt);
             }
         }
 #pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-            const float2 px = __half22float2(PX[p]), qx = __half22float2(QX[p]);
-            const float2 py = __half22float2(PY[p]), qy = __half22float2(QY[p]);
-            ax[2 * p] = fmaf(gdx, px.x, ax[2 * p]);
-            ax[2 * p + 1] = fmaf(gdx, px.y, ax[2 * p + 1]);
-            zx[2 * p] = fmaf(gdx, qx.x, zx[2 * p]);
-            zx[2 * p + 1] = fmaf(gdx, qx.y, zx[2 * p + 1]);
-            ay[2 * p] = fmaf(gdx, py.x, ay[2 * p]);
-            ay[2 * p + 1] = fmaf(gdx, py.y, ay[2 * p + 1]);
-            zy[2 * p] = fmaf(gdx, qy.x, zy[2 * p]);
-            zy[2 * p + 1] = fmaf(gdx, qy.y, zy[2 * p + 1]);
+        for (int j = 0; j < kStrip; ++j) {
+            const float2 pf = __half22float2(P[j]), qf = __half22float2(Q[j]);
+            A[j] = fma2(GD, pk(pf.x, pf.y), A[j]);
+            Z[j] = fma2(GD, pk(qf.x, qf.y), Z[j]);
         }
     }
-    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx,
-                sxs, ay, zy, sys, inv_kappa);
+    float ax[kStrip], zx[kStrip], ay[kStrip], zy[kStrip];
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        upk(A[j], ax[j], ay[j]);
+        upk(Z[j], zx[j], zy[j]);
+    }
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sxs, ay, zy, sys, inv_kappa);
 }
 
 template <int R, bool RANGE, int PREC>
