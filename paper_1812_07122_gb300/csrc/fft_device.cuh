@@ -5,7 +5,8 @@
 // every routine starts by assuming its input is visible to all threads (the caller synchronised)
 // and ends with a __syncthreads().
 //
-// Direct transforms (length L = product of the plan's radices 16, 8, 4, 2, 3, 5, 7):
+// Direct transforms (length L = product of the plan's radices 16, 15, 9, 8, 4, 2, 3, 5, 7;
+// 15 and 9 are two-level butterflies 3x5 and 3x3):
 //   forward: decimation in frequency, natural input -> output in digit-reversed order
 //            (frequency k at position perm[k]);
 //   inverse: the conjugate stages in reverse order, digit-reversed input -> natural output,
@@ -224,6 +225,104 @@ __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc, i
     }
 }
 
+// Two-level radix R = R1 x R2 (R1, R2 in {3, 5}): t = R2 t1 + t2, k = k1 + R1 k2.
+//   Y[t2][k1] = DFT_R1 over t1 of x[R2 t1 + t2];  Y[t2][k1] *= w_R^(t2 k1);
+//   y[k1 + R1 k2] = DFT_R2 over t2 of Y[t2][k1].
+// w_R^e = tw[e L / R] from the plan's twiddle table (L is a multiple of R). The result stays in
+// v with y[k] at v[two_level_slot<R1, R2>(k)], so no second register array is needed.
+template <int R1, int R2>
+__device__ __forceinline__ constexpr int two_level_slot(int k)
+{
+    return R2 * (k % R1) + k / R1;
+}
+
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void dft_two_level(float2 (&v)[R1 * R2], const float2* __restrict__ tw,
+                                              unsigned lr)
+{
+#pragma unroll
+    for (int t2 = 0; t2 < R2; ++t2) {
+        float2 a[R1];
+#pragma unroll
+        for (int t1 = 0; t1 < R1; ++t1) a[t1] = v[R2 * t1 + t2];
+        small_dft<R1, INV>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 y = a[k1];
+            if (t2 != 0 && k1 != 0) {
+                const float2 w = tw[(unsigned)(t2 * k1) * lr];
+                y = INV ? cmulc(y, w) : cmul(y, w);
+            }
+            v[R2 * k1 + t2] = y;
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 b[R2];
+#pragma unroll
+        for (int t2 = 0; t2 < R2; ++t2) b[t2] = v[R2 * k1 + t2];
+        small_dft<R2, INV>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[R2 * k1 + k2] = b[k2];
+    }
+}
+
+template <int R1, int R2>
+__device__ __forceinline__ void dif_stage2(float2* __restrict__ x, int lgc, int Lw, int m,
+                                           unsigned magic, int tw_step,
+                                           const float2* __restrict__ tw)
+{
+    constexpr int R = R1 * R2;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(Lw / R) << lgc;
+    const unsigned um = (unsigned)m, lblk = um * R, lr = (unsigned)(Lw / R);
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> lgc;
+        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
+        const unsigned j = bi - blk * um;
+        const unsigned base = blk * lblk + j;
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = x[((base + t * um) << lgc) + col];
+        dft_two_level<R1, R2, false>(v, tw, lr);
+        const unsigned jt = j * (unsigned)tw_step;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 y = v[two_level_slot<R1, R2>(q)];
+            x[((base + q * um) << lgc) + col] = q ? cmul(y, tw[q * jt]) : y;
+        }
+    }
+}
+
+template <int R1, int R2>
+__device__ __forceinline__ void dit_inv_stage2(float2* __restrict__ x, int lgc, int Lw, int m,
+                                               unsigned magic, int tw_step,
+                                               const float2* __restrict__ tw)
+{
+    constexpr int R = R1 * R2;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(Lw / R) << lgc;
+    const unsigned um = (unsigned)m, lblk = um * R, lr = (unsigned)(Lw / R);
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> lgc;
+        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
+        const unsigned j = bi - blk * um;
+        const unsigned base = blk * lblk + j;
+        const unsigned jt = j * (unsigned)tw_step;
+        float2 v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 a = x[((base + q * um) << lgc) + col];
+            v[q] = q ? cmulc(a, tw[q * jt]) : a;
+        }
+        dft_two_level<R1, R2, true>(v, tw, lr);
+#pragma unroll
+        for (int t = 0; t < R; ++t) x[((base + t * um) << lgc) + col] = v[two_level_slot<R1, R2>(t)];
+    }
+}
+
 __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlanDev& p,
                                                const float2* tw)
 {
@@ -234,6 +333,8 @@ __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlan
         const int tw_step = Lw / (m * R);
         switch (R) {
             case 16: dif_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 15: dif_stage2<3, 5>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 9: dif_stage2<3, 3>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 8: dif_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 4: dif_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 2: dif_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;
@@ -255,6 +356,8 @@ __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlan
         const int tw_step = Lw / (m * R);
         switch (R) {
             case 16: dit_inv_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 15: dit_inv_stage2<3, 5>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 9: dit_inv_stage2<3, 3>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 8: dit_inv_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 4: dit_inv_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
             case 2: dit_inv_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;

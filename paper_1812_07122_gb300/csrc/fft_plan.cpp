@@ -66,6 +66,8 @@ bool factor_direct(int N, std::vector<int>& radices)
     if (n % 8 == 0) { radices.push_back(8); n /= 8; }
     if (n % 4 == 0) { radices.push_back(4); n /= 4; }
     if (n % 2 == 0) { radices.push_back(2); n /= 2; }
+    while (n % 15 == 0) { radices.push_back(15); n /= 15; }
+    while (n % 9 == 0) { radices.push_back(9); n /= 9; }
     while (n % 3 == 0) { radices.push_back(3); n /= 3; }
     while (n % 5 == 0) { radices.push_back(5); n /= 5; }
     while (n % 7 == 0) { radices.push_back(7); n /= 7; }

@@ -31,6 +31,8 @@ namespace {
 
 // Shared-memory budget of one solve CTA; twiddles share it with the data when they fit.
 constexpr size_t kSmemCap = 220 * 1024;
+// Budget of each of two CTAs sharing an SM (228 KB per SM, 1 KB reserved per CTA).
+constexpr size_t kSmemPairCap = 112 * 1024;
 
 __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const FftPlanDev& p,
                                                         bool in_smem)
@@ -41,14 +43,12 @@ __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const F
     return tw_smem;
 }
 
-// K2 on one row pair, given its rows (in global or shared memory): r = D_x^T e_x + D_y^T e_y for
-// rows y0 and y1 packed as z = r0 + i r1, forward FFT, split into the two half spectra s0, s1.
-__device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, const float* eym,
-                                        const float* ey0, const float* ey1, bool has1, int W,
-                                        float2* s0, float2* s1, const FftPlanDev& rp,
-                                        const float2* tw, float2* data)
+// K2, first half: r = D_x^T e_x + D_y^T e_y for rows y0 and y1 (given in global or shared memory)
+// packed as z = r0 + i r1 into `data`.  Ends synchronised, so the rows may be overwritten after.
+__device__ __forceinline__ void k2_build(const float* ex0, const float* ex1, const float* eym,
+                                         const float* ey0, const float* ey1, bool has1, int W,
+                                         float2* data)
 {
-    const int Wh = W / 2 + 1;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int xm = (x == 0) ? W - 1 : x - 1;
         // (D_x^T e_x)[y][x] = e_x[y][x-1] - e_x[y][x];  (D_y^T e_y)[y][x] = e_y[y-1][x] - e_y[y][x]
@@ -58,6 +58,13 @@ __device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, cons
         data[x] = make_float2(r0, r1);
     }
     __syncthreads();
+}
+
+// K2, second half: forward FFT of z, split into the two half spectra s0, s1 (W/2+1 bins each).
+__device__ __forceinline__ void k2_transform(bool has1, int W, float2* s0, float2* s1,
+                                             const FftPlanDev& rp, const float2* tw, float2* data)
+{
+    const int Wh = W / 2 + 1;
     fft_forward(data, 0, rp, tw);
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
@@ -68,6 +75,16 @@ __device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, cons
         if (has1) s1[k] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
     }
     __syncthreads();
+}
+
+// K2 on one row pair: rows y0 and y1 packed as z = r0 + i r1, forward FFT, half spectra.
+__device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, const float* eym,
+                                        const float* ey0, const float* ey1, bool has1, int W,
+                                        float2* s0, float2* s1, const FftPlanDev& rp,
+                                        const float2* tw, float2* data)
+{
+    k2_build(ex0, ex1, eym, ey0, ey1, has1, W, data);
+    k2_transform(has1, W, s0, s1, rp, tw, data);
 }
 
 // K2: row pair `pair` (rows 2 pair, 2 pair + 1) of one channel, read from global memory.
@@ -134,12 +151,10 @@ __device__ __forceinline__ void k3_item(float2* __restrict__ spec, int H, int W,
     __syncthreads();
 }
 
-// K4 on one row pair, given its half spectra and input rows (global or shared memory):
-// rebuild Z = A + i B over all W bins, inverse FFT, u = f + result.
-__device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool has1,
-                                        const float* f0, const float* f1, float* o0, float* o1,
-                                        int W, const FftPlanDev& rp, const float2* tw,
-                                        float2* data)
+// K4, first half: rebuild Z = A + i B over all W bins of a row pair from its half spectra
+// (global or shared memory), in the digit-reversed order the inverse FFT reads.  Ends synchronised.
+__device__ __forceinline__ void k4_rebuild(const float2* s0, const float2* s1, bool has1, int W,
+                                           const FftPlanDev& rp, float2* data)
 {
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
         const bool upper = k > W / 2;
@@ -152,13 +167,29 @@ __device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool
         data[__ldg(rp.perm + k)] = make_float2(a.x - b.y, a.y + b.x);
     }
     __syncthreads();
-    fft_inverse(data, 0, rp, tw);
+}
+
+// K4, last step (after the inverse FFT): u = f + result, real part row a, imaginary part row b.
+__device__ __forceinline__ void k4_output(bool has1, const float* f0, const float* f1, float* o0,
+                                          float* o1, int W, const float2* data)
+{
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const float2 z = data[x];
         o0[x] = f0[x] + z.x;
         if (has1) o1[x] = f1[x] + z.y;
     }
     __syncthreads();
+}
+
+// K4 on one row pair: rebuild, inverse FFT, u = f + result.
+__device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool has1,
+                                        const float* f0, const float* f1, float* o0, float* o1,
+                                        int W, const FftPlanDev& rp, const float2* tw,
+                                        float2* data)
+{
+    k4_rebuild(s0, s1, has1, W, rp, data);
+    fft_inverse(data, 0, rp, tw);
+    k4_output(has1, f0, f1, o0, o1, W, data);
 }
 
 // K4: row pair `pair` of one channel, read from global memory.
@@ -257,135 +288,131 @@ __global__ void __launch_bounds__(512) k4_rows_inverse(
         k4_item(spec, f, out, H, W, pair, rp, tw, smem);
 }
 
-// ---- single image, staged: each CTA walks a contiguous band of items and copies the next item
-// into shared memory with cp.async while the current one is transformed. -----------------------
+// ---- single image, staged: each CTA walks a contiguous band of items.  Its input rows sit in
+// one staging buffer, which is refilled with cp.async for the next item as soon as the current
+// one has been read out of it, so the copy runs under the FFT.  256 threads (a 3840-point row
+// has 240 radix-16 or 256 radix-15 butterflies per stage) and two CTAs per SM. ------------------
 
-// Shared-memory layouts (bytes).
-__host__ __device__ __forceinline__ size_t k2s_stage_bytes(int W) { return align16(sizeof(float) * 4 * (size_t)W); }
+constexpr int kStagedThreads = 256;
+
+__host__ __device__ __forceinline__ size_t row_floats(int W) { return (size_t)((W + 3) & ~3); }
+// K2: [5][Wp] floats (e_x rows y0, y1; e_y rows y0-1, y0, y1), then the FFT buffer.
+__host__ __device__ __forceinline__ size_t k2s_stage_bytes(int W) { return sizeof(float) * 5 * row_floats(W); }
 __host__ __device__ __forceinline__ size_t k2s_smem(int W, int L)
 {
-    return 2 * k2s_stage_bytes(W) + align16(sizeof(float) * (size_t)W) + sizeof(float2) * (size_t)L;
+    return k2s_stage_bytes(W) + sizeof(float2) * (size_t)L;
 }
-__host__ __device__ __forceinline__ size_t k4s_stage_bytes(int W)
-{
-    return align16(sizeof(float2) * 2 * (size_t)(W / 2 + 1)) + align16(sizeof(float) * 2 * (size_t)W);
-}
+// K4: [2][Wh] half spectra, [2][Wp] floats of f, then the FFT buffer.
+__host__ __device__ __forceinline__ size_t k4s_spec_bytes(int W) { return align16(sizeof(float2) * 2 * (size_t)(W / 2 + 1)); }
 __host__ __device__ __forceinline__ size_t k4s_smem(int W, int L)
 {
-    return 2 * k4s_stage_bytes(W) + sizeof(float2) * (size_t)L;
+    return k4s_spec_bytes(W) + sizeof(float) * 2 * row_floats(W) + sizeof(float2) * (size_t)L;
 }
+// K3: two column blocks (double-buffered; the FFT runs in place in one of them).
 __host__ __device__ __forceinline__ size_t k3s_smem(int L, int lgc)
 {
     return 2 * (sizeof(float2) * (size_t)L << lgc);
 }
 
-__global__ void __launch_bounds__(512) k2_rows_staged(const float* __restrict__ ex,
-                                                      const float* __restrict__ ey,
-                                                      float2* __restrict__ spec, int H, int W,
-                                                      FftPlanDev rp, int vec)
+__global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float* __restrict__ ex,
+                                                                    const float* __restrict__ ey,
+                                                                    float2* __restrict__ spec,
+                                                                    int H, int W, FftPlanDev rp,
+                                                                    int vec)
 {
     extern __shared__ __align__(16) unsigned char staged_smem[];
-    unsigned char* smem = staged_smem;
-    float* stage = reinterpret_cast<float*>(smem);                       // [2][4][W]
-    const size_t sb = k2s_stage_bytes(W) / sizeof(float);
-    float* eyprev = reinterpret_cast<float*>(smem + 2 * k2s_stage_bytes(W));
-    float2* data = reinterpret_cast<float2*>(smem + 2 * k2s_stage_bytes(W) + align16(sizeof(float) * W));
+    float* st = reinterpret_cast<float*>(staged_smem);
+    const size_t Wp = row_floats(W);
+    float2* data = reinterpret_cast<float2*>(staged_smem + k2s_stage_bytes(W));
     const int Wh = W / 2 + 1;
     const int npairs = (H + 1) / 2;
     int p0, p1;
     band(npairs, p0, p1);
     if (p0 >= p1) return;
-    auto issue = [&](int p, float* st) {
+    auto issue = [&](int p) {
         const int y0 = 2 * p, y1 = y0 + 1;
+        const int ym = (y0 == 0) ? H - 1 : y0 - 1;
         stage_floats(st, ex + (size_t)y0 * W, W, vec);
-        stage_floats(st + 2 * W, ey + (size_t)y0 * W, W, vec);
+        stage_floats(st + 2 * Wp, ey + (size_t)ym * W, W, vec);
+        stage_floats(st + 3 * Wp, ey + (size_t)y0 * W, W, vec);
         if (y1 < H) {
-            stage_floats(st + W, ex + (size_t)y1 * W, W, vec);
-            stage_floats(st + 3 * W, ey + (size_t)y1 * W, W, vec);
+            stage_floats(st + Wp, ex + (size_t)y1 * W, W, vec);
+            stage_floats(st + 4 * Wp, ey + (size_t)y1 * W, W, vec);
         }
+        cp_commit();
     };
-    stage_floats(eyprev, ey + (size_t)(p0 == 0 ? H - 1 : 2 * p0 - 1) * W, W, vec);
-    issue(p0, stage);
-    cp_commit();
+    issue(p0);
     for (int p = p0; p < p1; ++p) {
-        float* st = stage + ((p - p0) & 1) * sb;
-        if (p + 1 < p1) {
-            issue(p + 1, stage + (((p - p0) & 1) ^ 1) * sb);
-            cp_commit();
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
+        cp_wait<0>();
         __syncthreads();
         const int y0 = 2 * p, y1 = y0 + 1;
         const bool has1 = y1 < H;
-        // k2_rows' first loop reads eyprev; its first barrier precedes the FFT, so eyprev can be
-        // refreshed (for the next pair) right after it returns.
-        k2_rows(st, st + W, eyprev, st + 2 * W, st + 3 * W, has1, W, spec + (size_t)y0 * Wh,
-                spec + (size_t)(has1 ? y1 : y0) * Wh, rp, rp.tw, data);
-        if (has1)
-            for (int x = threadIdx.x; x < W; x += blockDim.x) eyprev[x] = st[3 * W + x];
-        __syncthreads();
+        k2_build(st, st + Wp, st + 2 * Wp, st + 3 * Wp, st + 4 * Wp, has1, W, data);
+        if (p + 1 < p1) issue(p + 1);   // the rows of pair p have been read out
+        k2_transform(has1, W, spec + (size_t)y0 * Wh, spec + (size_t)(has1 ? y1 : y0) * Wh, rp,
+                     rp.tw, data);
     }
 }
 
-__global__ void __launch_bounds__(512) k4_rows_staged(const float2* __restrict__ spec,
-                                                      const float* f, float* out, int H, int W,
-                                                      FftPlanDev rp, int vec)
+__global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2* __restrict__ spec,
+                                                                    const float* f, float* out,
+                                                                    int H, int W, FftPlanDev rp,
+                                                                    int vec)
 {
     extern __shared__ __align__(16) unsigned char staged_smem[];
-    unsigned char* smem = staged_smem;
     const int Wh = W / 2 + 1;
-    const size_t sb = k4s_stage_bytes(W);
-    const size_t so = align16(sizeof(float2) * 2 * (size_t)Wh);    // f rows after the spectra
-    float2* data = reinterpret_cast<float2*>(smem + 2 * sb);
+    const size_t Wp = row_floats(W);
+    float2* ss = reinterpret_cast<float2*>(staged_smem);
+    float* sf = reinterpret_cast<float*>(staged_smem + k4s_spec_bytes(W));
+    float2* data = reinterpret_cast<float2*>(staged_smem + k4s_spec_bytes(W) + sizeof(float) * 2 * Wp);
     const int npairs = (H + 1) / 2;
     int p0, p1;
     band(npairs, p0, p1);
     if (p0 >= p1) return;
-    auto issue = [&](int p, unsigned char* st) {
+    auto issue_spec = [&](int p) {
         const int y0 = 2 * p, y1 = y0 + 1;
-        float2* ss = reinterpret_cast<float2*>(st);
-        float* sf = reinterpret_cast<float*>(st + so);
         stage_complex(ss, spec + (size_t)y0 * Wh, Wh);
-        stage_floats(sf, f + (size_t)y0 * W, W, vec);
-        if (y1 < H) {
-            stage_complex(ss + Wh, spec + (size_t)y1 * Wh, Wh);
-            stage_floats(sf + W, f + (size_t)y1 * W, W, vec);
-        }
+        if (y1 < H) stage_complex(ss + Wh, spec + (size_t)y1 * Wh, Wh);
+        cp_commit();
     };
-    issue(p0, smem);
-    cp_commit();
+    auto issue_f = [&](int p) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        stage_floats(sf, f + (size_t)y0 * W, W, vec);
+        if (y1 < H) stage_floats(sf + Wp, f + (size_t)y1 * W, W, vec);
+        cp_commit();
+    };
+    // Copy groups complete in issue order: spectra(p), f(p), spectra(p+1), f(p+1), ...
+    issue_spec(p0);
+    issue_f(p0);
     for (int p = p0; p < p1; ++p) {
-        unsigned char* st = smem + ((p - p0) & 1) * sb;
-        if (p + 1 < p1) {
-            issue(p + 1, smem + (((p - p0) & 1) ^ 1) * sb);
-            cp_commit();
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
+        cp_wait<1>();                 // spectra(p) landed; f(p) may still be in flight
         __syncthreads();
         const int y0 = 2 * p, y1 = y0 + 1;
         const bool has1 = y1 < H;
-        const float2* ss = reinterpret_cast<const float2*>(st);
-        const float* sf = reinterpret_cast<const float*>(st + so);
-        k4_rows(ss, ss + Wh, has1, sf, sf + W, out + (size_t)y0 * W,
-                out + (size_t)(has1 ? y1 : y0) * W, W, rp, rp.tw, data);
+        k4_rebuild(ss, ss + Wh, has1, W, rp, data);
+        const bool more = p + 1 < p1;
+        if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
+        fft_inverse(data, 0, rp, rp.tw);
+        if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
+        __syncthreads();
+        k4_output(has1, sf, sf + Wp, out + (size_t)y0 * W, out + (size_t)(has1 ? y1 : y0) * W, W,
+                  data);
+        if (more) issue_f(p + 1);
     }
 }
 
-__global__ void __launch_bounds__(512) k3_cols_staged(float2* __restrict__ spec, int H, int W,
-                                                      FftPlanDev cp, const float* __restrict__ sx,
-                                                      const float* __restrict__ sy, float lam,
-                                                      float scale, int lgc)
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k3_cols_staged(float2* __restrict__ spec, int H,
+                                                                int W, FftPlanDev cp,
+                                                                const float* __restrict__ sx,
+                                                                const float* __restrict__ sy,
+                                                                float lam, float scale, int lgc)
 {
     extern __shared__ __align__(16) unsigned char staged_smem[];
-    unsigned char* smem = staged_smem;
     const int CB = 1 << lgc;
     const int Wh = W / 2 + 1;
     const size_t blk_elems = (size_t)cp.L << lgc;
-    float2* bufs = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(staged_smem);
     const int nblk = (Wh + CB - 1) >> lgc;
     int b0, b1;
     band(nblk, b0, b1);
@@ -498,7 +525,8 @@ void init_solve_kernel_attributes()
     cudaFuncSetAttribute(k3_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k2_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -531,8 +559,8 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
 {
     const int H = p.H, W = p.W;
     const float scale = 1.0f / ((float)H * (float)W);
-    // Staged drivers when their double-buffered shared memory fits; rows of floats are copied
-    // 16 bytes at a time when every row start is 16-byte aligned.
+    // Staged drivers when their shared memory fits; rows of floats are copied 16 bytes at a time
+    // when every row start is 16-byte aligned.
     const size_t cap = kSmemCap;
     const bool al16 = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(ex) | reinterpret_cast<uintptr_t>(ey) |
                                         reinterpret_cast<uintptr_t>(f)) % 16 == 0);
@@ -547,9 +575,9 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     if (rows_staged) {
         const size_t sm2 = k2s_smem(W, rp.L);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_staged, 512, sm2);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_staged, kStagedThreads, sm2);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
-        k2_rows_staged<<<grid, 512, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
+        k2_rows_staged<<<grid, kStagedThreads, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
         const int tw_r = smem_r > sizeof(float2) * rp.L;
@@ -561,12 +589,15 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     }
     if (marks) cudaEventRecord(marks[0], s);
     if (cols_staged) {
+        // Two 256-thread CTAs per SM when two double-buffered blocks fit, else one of 512.
         const size_t sm3 = k3s_smem(cp.L, lgc);
-        const int thr = threads_for((cp.L * CB) / 4);
+        const bool pair = sm3 <= kSmemPairCap;
+        const int thr = pair ? 256 : 512;
+        auto kern = pair ? k3_cols_staged<256, 2> : k3_cols_staged<512, 1>;
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_cols_staged, thr, sm3);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, thr, sm3);
         const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
-        k3_cols_staged<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc);
+        kern<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc);
     } else {
         const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
         const int CB1 = 1 << lgc1;
@@ -583,9 +614,9 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     if (rows_staged) {
         const size_t sm4 = k4s_smem(W, rp.L);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_staged, 512, sm4);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_staged, kStagedThreads, sm4);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
-        k4_rows_staged<<<grid, 512, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
+        k4_rows_staged<<<grid, kStagedThreads, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
         const int tw_r = smem_r > sizeof(float2) * rp.L;
