@@ -167,162 +167,191 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R])
     }
 }
 
-// One decimation-in-frequency stage over blocks of length R*m:
-//   inputs x[base + t m], base = blk*(R m) + j;  R-point DFT;  output q times w_(R m)^(j q).
-// blk = b / m comes from a multiply-high by the plan's magic number (no integer division).
-template <int R>
-__device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc, int Lw, int m,
-                                          unsigned magic, int tw_step,
-                                          const float2* __restrict__ tw)
+// cos and sin of 2 pi e / R for the internal twiddles of the two-level butterflies
+// (R = 15: e = 1, 2, 3, 4, 6, 8; R = 9: e = 1, 2, 4; mathematical constants).
+__device__ __forceinline__ constexpr float root2_cos(int R, int e)
 {
-    const unsigned mask = (1u << lgc) - 1u;
-    const unsigned total = (unsigned)(Lw / R) << lgc;
-    const unsigned um = (unsigned)m, lblk = um * R;
-    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
-        const unsigned col = b & mask;
-        const unsigned bi = b >> lgc;
-        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
-        const unsigned j = bi - blk * um;
-        const unsigned base = blk * lblk + j;
-        float2 v[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = x[((base + t * um) << lgc) + col];
-        small_dft<R, false>(v);
-        const unsigned jt = j * (unsigned)tw_step;
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const float2 w = q ? tw[q * jt] : make_float2(1.f, 0.f);
-            x[((base + q * um) << lgc) + col] = q ? cmul(v[q], w) : v[q];
-        }
-    }
+    return R == 15 ? (e == 1 ? 0.913545457642600895502f : e == 2 ? 0.669130606358858213826f
+                    : e == 3 ? 0.309016994374947424102f : e == 4 ? -0.104528463267653471400f
+                    : e == 6 ? -0.809016994374947424102f : -0.978147600733805637929f)
+                   : (e == 1 ? 0.766044443118978035202f : e == 2 ? 0.173648177666930348852f
+                    : -0.939692620785908384054f);
 }
-
-// The inverse of dif_stage (up to the factor R): inputs times conj(w_(R m)^(j q)), inverse DFT.
-template <int R>
-__device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc, int Lw, int m,
-                                              unsigned magic, int tw_step,
-                                              const float2* __restrict__ tw)
+__device__ __forceinline__ constexpr float root2_sin(int R, int e)
 {
-    const unsigned mask = (1u << lgc) - 1u;
-    const unsigned total = (unsigned)(Lw / R) << lgc;
-    const unsigned um = (unsigned)m, lblk = um * R;
-    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
-        const unsigned col = b & mask;
-        const unsigned bi = b >> lgc;
-        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
-        const unsigned j = bi - blk * um;
-        const unsigned base = blk * lblk + j;
-        const unsigned jt = j * (unsigned)tw_step;
-        float2 v[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const float2 a = x[((base + q * um) << lgc) + col];
-            v[q] = q ? cmulc(a, tw[q * jt]) : a;
-        }
-        small_dft<R, true>(v);
-#pragma unroll
-        for (int t = 0; t < R; ++t) x[((base + t * um) << lgc) + col] = v[t];
-    }
+    return R == 15 ? (e == 1 ? 0.406736643075800207754f : e == 2 ? 0.743144825477394235015f
+                    : e == 3 ? 0.951056516295153572116f : e == 4 ? 0.994521895368273336923f
+                    : e == 6 ? 0.587785252292473129169f : -0.207911690817759337102f)
+                   : (e == 1 ? 0.642787609686539326323f : e == 2 ? 0.984807753012208059367f
+                    : 0.342020143325668733044f);
 }
 
 // Two-level radix R = R1 x R2 (R1, R2 in {3, 5}): t = R2 t1 + t2, k = k1 + R1 k2.
 //   Y[t2][k1] = DFT_R1 over t1 of x[R2 t1 + t2];  Y[t2][k1] *= w_R^(t2 k1);
 //   y[k1 + R1 k2] = DFT_R2 over t2 of Y[t2][k1].
-// w_R^e = tw[e L / R] from the plan's twiddle table (L is a multiple of R). The result stays in
-// v with y[k] at v[two_level_slot<R1, R2>(k)], so no second register array is needed.
+// The result stays in v with y[k] at v[slot(k)], so no second register array is needed.
 template <int R1, int R2>
-__device__ __forceinline__ constexpr int two_level_slot(int k)
-{
-    return R2 * (k % R1) + k / R1;
-}
-
-template <int R1, int R2, bool INV>
-__device__ __forceinline__ void dft_two_level(float2 (&v)[R1 * R2], const float2* __restrict__ tw,
-                                              unsigned lr)
-{
+struct TwoLevel {
+    static constexpr int R = R1 * R2;
+    static constexpr int F = R1;   // outer twiddles from w^e and w^(R1 e), see twiddle_powers
+    static __device__ __forceinline__ constexpr int slot(int k) { return R2 * (k % R1) + k / R1; }
+    template <bool INV>
+    static __device__ __forceinline__ void dft(float2 (&v)[R])
+    {
 #pragma unroll
-    for (int t2 = 0; t2 < R2; ++t2) {
-        float2 a[R1];
+        for (int t2 = 0; t2 < R2; ++t2) {
+            float2 a[R1];
 #pragma unroll
-        for (int t1 = 0; t1 < R1; ++t1) a[t1] = v[R2 * t1 + t2];
-        small_dft<R1, INV>(a);
+            for (int t1 = 0; t1 < R1; ++t1) a[t1] = v[R2 * t1 + t2];
+            small_dft<R1, INV>(a);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                float2 y = a[k1];
+                if (t2 != 0 && k1 != 0) {
+                    const int e = t2 * k1;   // w_R^e = (cos, -sin) forward, (cos, sin) inverse
+                    const float2 w = make_float2(root2_cos(R, e), root2_sin(R, e));
+                    y = INV ? cmul(y, w) : cmulc(y, w);
+                }
+                v[R2 * k1 + t2] = y;
+            }
+        }
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) {
-            float2 y = a[k1];
-            if (t2 != 0 && k1 != 0) {
-                const float2 w = tw[(unsigned)(t2 * k1) * lr];
-                y = INV ? cmulc(y, w) : cmul(y, w);
+            float2 b[R2];
+#pragma unroll
+            for (int t2 = 0; t2 < R2; ++t2) b[t2] = v[R2 * k1 + t2];
+            small_dft<R2, INV>(b);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) v[R2 * k1 + k2] = b[k2];
+        }
+    }
+};
+
+// A plain R-point butterfly in the same interface (output k at v[k]).
+template <int R_>
+struct OneLevel {
+    static constexpr int R = R_;
+    // outer twiddles from w^e and w^(4 e) for R = 4, 8, 16; table loads for the small odd radices
+    static constexpr int F = (R_ == 4 || R_ == 8 || R_ == 16) ? 4 : 0;
+    static __device__ __forceinline__ constexpr int slot(int k) { return k; }
+    template <bool INV>
+    static __device__ __forceinline__ void dft(float2 (&v)[R]) { small_dft<R, INV>(v); }
+};
+
+// Outer twiddles w^(e q), q = 0..R-1, of one butterfly.  With F > 0 only two table entries are
+// read, a = w^e and b = w^(F e), and w^(e q) = a^(q mod F) * b^(q div F): each is a product of
+// at most four rounded factors (a few ulps), and the table reads drop from R-1 to 2.  With F = 0
+// every w^(e q) is read from the table.  e < L / R, so F e < L stays inside the table.
+template <int R, int F>
+__device__ __forceinline__ void twiddle_powers(float2 (&w)[R], const float2* __restrict__ tw,
+                                               unsigned e)
+{
+    if constexpr (F == 0) {
+        w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int q = 1; q < R; ++q) w[q] = tw[q * e];
+    } else {
+        constexpr int G = (R + F - 1) / F;
+        float2 ap[F], bp[G];
+        ap[0] = make_float2(1.f, 0.f);
+        ap[1] = tw[e];
+#pragma unroll
+        for (int k = 2; k < F; ++k) ap[k] = (k % 2 == 0) ? cmul(ap[k / 2], ap[k / 2]) : cmul(ap[k - 1], ap[1]);
+        bp[0] = make_float2(1.f, 0.f);
+        if constexpr (G > 1) {
+            bp[1] = tw[F * e];
+#pragma unroll
+            for (int k = 2; k < G; ++k) bp[k] = (k % 2 == 0) ? cmul(bp[k / 2], bp[k / 2]) : cmul(bp[k - 1], bp[1]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int k1 = q % F, k2 = q / F;
+            w[q] = k2 == 0 ? ap[k1] : k1 == 0 ? bp[k2] : cmul(ap[k1], bp[k2]);
+        }
+    }
+}
+
+// One decimation-in-frequency stage over blocks of length R*m:
+//   inputs x[base + t m], base = blk*(R m) + j;  R-point DFT;  output q times w_(R m)^(j q).
+// blk = b / m comes from a multiply-high by the plan's magic number (no integer division).
+// The last stage (m = 1) has j = 0, so its twiddles are all 1 and are skipped.
+// LGC >= 0 fixes the column-set shift at compile time; LGC = -1 takes it from `lgc_rt`.
+template <class B, int LGC>
+__device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, int Lw, int m,
+                                          unsigned magic, int tw_step,
+                                          const float2* __restrict__ tw)
+{
+    constexpr int R = B::R;
+    const int lgc = LGC >= 0 ? LGC : lgc_rt;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(Lw / R) << lgc;
+    const unsigned um = (unsigned)m, lblk = um * R;
+    const bool twiddled = m > 1;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> lgc;
+        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
+        const unsigned j = bi - blk * um;
+        float2* xb = x + (((blk * lblk + j) << lgc) + col);
+        const unsigned st = um << lgc;
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = xb[t * st];
+        B::template dft<false>(v);
+        if (twiddled) {
+            float2 w[R];
+            twiddle_powers<R, B::F>(w, tw, j * (unsigned)tw_step);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const float2 y = v[B::slot(q)];
+                xb[q * st] = q ? cmul(y, w[q]) : y;
             }
-            v[R2 * k1 + t2] = y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) xb[q * st] = v[B::slot(q)];
         }
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) {
-        float2 b[R2];
-#pragma unroll
-        for (int t2 = 0; t2 < R2; ++t2) b[t2] = v[R2 * k1 + t2];
-        small_dft<R2, INV>(b);
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) v[R2 * k1 + k2] = b[k2];
     }
 }
 
-template <int R1, int R2>
-__device__ __forceinline__ void dif_stage2(float2* __restrict__ x, int lgc, int Lw, int m,
-                                           unsigned magic, int tw_step,
-                                           const float2* __restrict__ tw)
+// The inverse of dif_stage (up to the factor R): inputs times conj(w_(R m)^(j q)), inverse DFT.
+template <class B, int LGC>
+__device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt, int Lw, int m,
+                                              unsigned magic, int tw_step,
+                                              const float2* __restrict__ tw)
 {
-    constexpr int R = R1 * R2;
+    constexpr int R = B::R;
+    const int lgc = LGC >= 0 ? LGC : lgc_rt;
     const unsigned mask = (1u << lgc) - 1u;
     const unsigned total = (unsigned)(Lw / R) << lgc;
-    const unsigned um = (unsigned)m, lblk = um * R, lr = (unsigned)(Lw / R);
+    const unsigned um = (unsigned)m, lblk = um * R;
+    const bool twiddled = m > 1;
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> lgc;
         const unsigned blk = magic ? __umulhi(bi, magic) : bi;
         const unsigned j = bi - blk * um;
-        const unsigned base = blk * lblk + j;
+        float2* xb = x + (((blk * lblk + j) << lgc) + col);
+        const unsigned st = um << lgc;
         float2 v[R];
+        if (twiddled) {
+            float2 w[R];
+            twiddle_powers<R, B::F>(w, tw, j * (unsigned)tw_step);
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = x[((base + t * um) << lgc) + col];
-        dft_two_level<R1, R2, false>(v, tw, lr);
-        const unsigned jt = j * (unsigned)tw_step;
+            for (int q = 0; q < R; ++q) {
+                const float2 a = xb[q * st];
+                v[q] = q ? cmulc(a, w[q]) : a;
+            }
+        } else {
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const float2 y = v[two_level_slot<R1, R2>(q)];
-            x[((base + q * um) << lgc) + col] = q ? cmul(y, tw[q * jt]) : y;
+            for (int q = 0; q < R; ++q) v[q] = xb[q * st];
         }
+        B::template dft<true>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) xb[t * st] = v[B::slot(t)];
     }
 }
 
-template <int R1, int R2>
-__device__ __forceinline__ void dit_inv_stage2(float2* __restrict__ x, int lgc, int Lw, int m,
-                                               unsigned magic, int tw_step,
-                                               const float2* __restrict__ tw)
-{
-    constexpr int R = R1 * R2;
-    const unsigned mask = (1u << lgc) - 1u;
-    const unsigned total = (unsigned)(Lw / R) << lgc;
-    const unsigned um = (unsigned)m, lblk = um * R, lr = (unsigned)(Lw / R);
-    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
-        const unsigned col = b & mask;
-        const unsigned bi = b >> lgc;
-        const unsigned blk = magic ? __umulhi(bi, magic) : bi;
-        const unsigned j = bi - blk * um;
-        const unsigned base = blk * lblk + j;
-        const unsigned jt = j * (unsigned)tw_step;
-        float2 v[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const float2 a = x[((base + q * um) << lgc) + col];
-            v[q] = q ? cmulc(a, tw[q * jt]) : a;
-        }
-        dft_two_level<R1, R2, true>(v, tw, lr);
-#pragma unroll
-        for (int t = 0; t < R; ++t) x[((base + t * um) << lgc) + col] = v[two_level_slot<R1, R2>(t)];
-    }
-}
-
+template <int LGC>
 __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlanDev& p,
                                                const float2* tw)
 {
@@ -332,20 +361,21 @@ __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlan
         const unsigned mg = p.magic[s];
         const int tw_step = Lw / (m * R);
         switch (R) {
-            case 16: dif_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 15: dif_stage2<3, 5>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 9: dif_stage2<3, 3>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 8: dif_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 4: dif_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 2: dif_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 3: dif_stage<3>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 5: dif_stage<5>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            default: dif_stage<7>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 16: dif_stage<OneLevel<16>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 15: dif_stage<TwoLevel<3, 5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 9: dif_stage<TwoLevel<3, 3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 8: dif_stage<OneLevel<8>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 4: dif_stage<OneLevel<4>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 2: dif_stage<OneLevel<2>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 3: dif_stage<OneLevel<3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 5: dif_stage<OneLevel<5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            default: dif_stage<OneLevel<7>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
         }
         __syncthreads();
     }
 }
 
+template <int LGC>
 __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlanDev& p,
                                                const float2* tw)
 {
@@ -355,15 +385,15 @@ __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlan
         const unsigned mg = p.magic[s];
         const int tw_step = Lw / (m * R);
         switch (R) {
-            case 16: dit_inv_stage<16>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 15: dit_inv_stage2<3, 5>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 9: dit_inv_stage2<3, 3>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 8: dit_inv_stage<8>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 4: dit_inv_stage<4>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 2: dit_inv_stage<2>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 3: dit_inv_stage<3>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 5: dit_inv_stage<5>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            default: dit_inv_stage<7>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 16: dit_inv_stage<OneLevel<16>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 15: dit_inv_stage<TwoLevel<3, 5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 9: dit_inv_stage<TwoLevel<3, 3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 8: dit_inv_stage<OneLevel<8>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 4: dit_inv_stage<OneLevel<4>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 2: dit_inv_stage<OneLevel<2>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 3: dit_inv_stage<OneLevel<3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 5: dit_inv_stage<OneLevel<5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            default: dit_inv_stage<OneLevel<7>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
         }
         __syncthreads();
     }
@@ -371,11 +401,11 @@ __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlan
 
 // Bluestein: X_k = c_k sum_n (x_n c_n) conj(c_{k-n}),  c_n = exp(-i pi n^2 / N).
 // The inverse transform conjugates input and output.
-template <bool INV>
+template <bool INV, int LGC>
 __device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& p,
                                           const float2* tw)
 {
-    const int ncols = 1 << lgc;
+    if (LGC >= 0) lgc = LGC;
     const int N = p.N, Lw = p.L;
     for (int i = threadIdx.x; i < (Lw << lgc); i += blockDim.x) {
         const int n = i >> lgc;
@@ -388,33 +418,35 @@ __device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& 
         x[i] = v;
     }
     __syncthreads();
-    direct_forward(x, lgc, p, tw);
+    direct_forward<LGC>(x, lgc, p, tw);
     for (int i = threadIdx.x; i < (Lw << lgc); i += blockDim.x)
         x[i] = cmul(x[i], __ldg(p.bhat + (i >> lgc)));
     __syncthreads();
-    direct_inverse(x, lgc, p, tw);
+    direct_inverse<LGC>(x, lgc, p, tw);
     for (int i = threadIdx.x; i < (N << lgc); i += blockDim.x) {
         const float2 v = cmul(x[i], __ldg(p.chirp + (i >> lgc)));
         x[i] = INV ? cconj(v) : v;
     }
     __syncthreads();
-    (void)ncols;
 }
 
 // Forward DFT of every column: natural input; frequency k ends at position perm[k].
+// LGC >= 0 fixes lgc at compile time (rows: 0); LGC = -1 reads it at run time.
+template <int LGC = -1>
 __device__ __forceinline__ void fft_forward(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
-    if (p.bluestein) bluestein<false>(x, lgc, p, tw);
-    else direct_forward(x, lgc, p, tw);
+    if (p.bluestein) bluestein<false, LGC>(x, lgc, p, tw);
+    else direct_forward<LGC>(x, lgc, p, tw);
 }
 
 // Unnormalised inverse DFT: frequency k read from position perm[k]; natural output.
+template <int LGC = -1>
 __device__ __forceinline__ void fft_inverse(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
-    if (p.bluestein) bluestein<true>(x, lgc, p, tw);
-    else direct_inverse(x, lgc, p, tw);
+    if (p.bluestein) bluestein<true, LGC>(x, lgc, p, tw);
+    else direct_inverse<LGC>(x, lgc, p, tw);
 }
 
 }  // namespace blfls

@@ -31,8 +31,6 @@ namespace {
 
 // Shared-memory budget of one solve CTA; twiddles share it with the data when they fit.
 constexpr size_t kSmemCap = 220 * 1024;
-// Budget of each of two CTAs sharing an SM (228 KB per SM, 1 KB reserved per CTA).
-constexpr size_t kSmemPairCap = 112 * 1024;
 
 __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const FftPlanDev& p,
                                                         bool in_smem)
@@ -65,7 +63,7 @@ __device__ __forceinline__ void k2_transform(bool has1, int W, float2* s0, float
                                              const FftPlanDev& rp, const float2* tw, float2* data)
 {
     const int Wh = W / 2 + 1;
-    fft_forward(data, 0, rp, tw);
+    fft_forward<0>(data, 0, rp, tw);
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
         const float2 zk = data[__ldg(rp.perm + k)];
@@ -105,6 +103,7 @@ __device__ __forceinline__ void k2_item(const float* __restrict__ ex, const floa
 // K3 on one column block already in `data` (rows n < H; the caller synchronised): forward FFT
 // down the columns, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the 1/(HW) of the
 // inverse), inverse FFT.  Ends synchronised.
+template <int LGC = -1>
 __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int kx0, int lgc,
                                                const FftPlanDev& cp, const float* __restrict__ sx,
                                                const float* __restrict__ sy, float lam,
@@ -112,7 +111,8 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
 {
     const int CB = 1 << lgc;
     const int Wh = W / 2 + 1;
-    fft_forward(data, lgc, cp, tw);
+    if (LGC >= 0) lgc = LGC;
+    fft_forward<LGC>(data, lgc, cp, tw);
     const int nfreq = cp.bluestein ? H : cp.L;
     for (int i = threadIdx.x; i < (nfreq << lgc); i += blockDim.x) {
         const int p = i >> lgc, c = i & (CB - 1);
@@ -124,7 +124,7 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
         data[i] = make_float2(v.x * m, v.y * m);
     }
     __syncthreads();
-    fft_inverse(data, lgc, cp, tw);
+    fft_inverse<LGC>(data, lgc, cp, tw);
 }
 
 // K3: columns [blk * 2^lgc, (blk + 1) * 2^lgc) of the half spectrum of one channel.
@@ -188,7 +188,7 @@ __device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool
                                         float2* data)
 {
     k4_rebuild(s0, s1, has1, W, rp, data);
-    fft_inverse(data, 0, rp, tw);
+    fft_inverse<0>(data, 0, rp, tw);
     k4_output(has1, f0, f1, o0, o1, W, data);
 }
 
@@ -308,10 +308,11 @@ __host__ __device__ __forceinline__ size_t k4s_smem(int W, int L)
 {
     return k4s_spec_bytes(W) + sizeof(float) * 2 * row_floats(W) + sizeof(float2) * (size_t)L;
 }
-// K3: two column blocks (double-buffered; the FFT runs in place in one of them).
+// K3: two column blocks (double-buffered; the FFT runs in place in one of them), then the
+// plan's twiddle table.
 __host__ __device__ __forceinline__ size_t k3s_smem(int L, int lgc)
 {
-    return 2 * (sizeof(float2) * (size_t)L << lgc);
+    return 2 * (sizeof(float2) * (size_t)L << lgc) + sizeof(float2) * (size_t)L;
 }
 
 __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float* __restrict__ ex,
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
         k4_rebuild(ss, ss + Wh, has1, W, rp, data);
         const bool more = p + 1 < p1;
         if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
-        fft_inverse(data, 0, rp, rp.tw);
+        fft_inverse<0>(data, 0, rp, rp.tw);
         if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
         __syncthreads();
         k4_output(has1, sf, sf + Wp, out + (size_t)y0 * W, out + (size_t)(has1 ? y1 : y0) * W, W,
@@ -401,18 +402,23 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
     }
 }
 
-template <int THREADS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k3_cols_staged(float2* __restrict__ spec, int H,
-                                                                int W, FftPlanDev cp,
-                                                                const float* __restrict__ sx,
-                                                                const float* __restrict__ sy,
-                                                                float lam, float scale, int lgc)
+// Launched with any block size up to kColThreadsMax (chosen per plan, see col_threads).
+constexpr int kColThreadsMax = 576;
+
+template <int LGC>
+__global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restrict__ spec, int H,
+                                                                 int W, FftPlanDev cp,
+                                                                 const float* __restrict__ sx,
+                                                                 const float* __restrict__ sy,
+                                                                 float lam, float scale)
 {
+    constexpr int lgc = LGC;
     extern __shared__ __align__(16) unsigned char staged_smem[];
     const int CB = 1 << lgc;
     const int Wh = W / 2 + 1;
     const size_t blk_elems = (size_t)cp.L << lgc;
     float2* bufs = reinterpret_cast<float2*>(staged_smem);
+    float2* tws = bufs + 2 * blk_elems;
     const int nblk = (Wh + CB - 1) >> lgc;
     int b0, b1;
     band(nblk, b0, b1);
@@ -428,6 +434,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k3_cols_staged(float2* __restri
     };
     issue(b0, bufs);
     cp_commit();
+    for (int i = threadIdx.x; i < cp.L; i += blockDim.x) tws[i] = __ldg(cp.tw + i);
     for (int b = b0; b < b1; ++b) {
         float2* data = bufs + ((b - b0) & 1) * blk_elems;
         if (b + 1 < b1) {
@@ -439,7 +446,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k3_cols_staged(float2* __restri
         }
         __syncthreads();
         const int kx0 = b * CB;
-        k3_solve_block(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, cp.tw);
+        k3_solve_block<LGC>(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tws);
         for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
             const int n = i >> lgc, c = i & (CB - 1);
             const int kx = kx0 + c;
@@ -525,8 +532,11 @@ void init_solve_kernel_attributes()
     cudaFuncSetAttribute(k3_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k2_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k3_cols_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -550,6 +560,43 @@ int solve_fit_lgc(int L, int col_block)
     while ((1 << lgc) < col_block) ++lgc;
     while (lgc > 0 && sizeof(float2) * (size_t)L * (1u << lgc) > kSmemCap) --lgc;
     return lgc;
+}
+
+// Block size of the staged column driver.  Stage s of the plan has (L / radix_s) << lgc
+// butterflies and every thread takes ceil(butterflies / threads) of them, so a block size that
+// leaves a few butterflies over doubles that stage.  Pick the size (a multiple of 32 up to
+// kColThreadsMax) with the least sum over stages of ceil(butterflies / threads) divided by the
+// number of CTAs that fit on an SM.
+typedef void (*ColsStagedFn)(float2*, int, int, FftPlanDev, const float*, const float*, float, float);
+static ColsStagedFn cols_staged_kernel(int lgc)
+{
+    switch (lgc) {
+        case 0: return k3_cols_staged<0>;
+        case 1: return k3_cols_staged<1>;
+        case 2: return k3_cols_staged<2>;
+        case 3: return k3_cols_staged<3>;
+        default: return k3_cols_staged<4>;   // col_block is at most 16
+    }
+}
+
+static int col_threads(const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
+{
+    int best_t = 128, best_occ = 1;
+    double best = 1e30;
+    for (int t = 128; t <= kColThreadsMax; t += 32) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cols_staged_kernel(lgc), t, smem);
+        if (occ < 1) continue;
+        long rounds = 0;
+        for (int st = 0; st < cp.nst; ++st) {
+            const long nb = (long)(cp.L / cp.radix[st]) << lgc;
+            rounds += (nb + t - 1) / t;
+        }
+        const double cost = (double)rounds / occ;
+        if (cost < best - 1e-9) { best = cost; best_t = t; best_occ = occ; }
+    }
+    *occ_out = best_occ;
+    return best_t;
 }
 
 cudaError_t launch_solve_residual(const float* f, const float* ex, const float* ey, float* out,
@@ -589,15 +636,11 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     }
     if (marks) cudaEventRecord(marks[0], s);
     if (cols_staged) {
-        // Two 256-thread CTAs per SM when two double-buffered blocks fit, else one of 512.
         const size_t sm3 = k3s_smem(cp.L, lgc);
-        const bool pair = sm3 <= kSmemPairCap;
-        const int thr = pair ? 256 : 512;
-        auto kern = pair ? k3_cols_staged<256, 2> : k3_cols_staged<512, 1>;
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, thr, sm3);
+        const int thr = col_threads(cp, lgc, sm3, &occ);
         const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
-        kern<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale, lgc);
+        cols_staged_kernel(lgc)<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
     } else {
         const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
         const int CB1 = 1 << lgc1;
