@@ -246,7 +246,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
                 P.total_rows += j.C * ((j.H + 1) / 2);
                 P.cols.push_back(make_int2(entry, P.total_cols));
                 P.total_cols += j.C * ((j.W / 2 + 1 + (1 << I.lgc) - 1) >> I.lgc);
-                P.smem_rows = std::max(P.smem_rows, sizeof(float2) * (size_t)I.rp->L);
+                P.smem_rows = std::max(P.smem_rows, sizeof(float2) * (size_t)row_buf_elems(*I.rp));
                 P.smem_cols = std::max(P.smem_cols, (sizeof(float2) * (size_t)I.cp->L) << I.lgc);
             }
             max_groups = std::max(max_groups, (int)P.groups.size());

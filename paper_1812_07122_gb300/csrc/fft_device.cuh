@@ -276,10 +276,12 @@ __device__ __forceinline__ void twiddle_powers(float2 (&w)[R], const float2* __r
 // blk = b / m comes from a multiply-high by the plan's magic number (no integer division).
 // The last stage (m = 1) has j = 0, so its twiddles are all 1 and are skipped.
 // LGC >= 0 fixes the column-set shift at compile time; LGC = -1 takes it from `lgc_rt`.
-template <class B, int LGC>
+// PAD (rows, lgc = 0) addresses a row buffer padded as described at FftPlanDev::pad_span.
+template <class B, int LGC, bool PAD>
 __device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, int Lw, int m,
                                           unsigned magic, int tw_step,
-                                          const float2* __restrict__ tw)
+                                          const float2* __restrict__ tw, int pad_span,
+                                          unsigned pad_magic)
 {
     constexpr int R = B::R;
     const int lgc = LGC >= 0 ? LGC : lgc_rt;
@@ -287,13 +289,19 @@ __device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, in
     const unsigned total = (unsigned)(Lw / R) << lgc;
     const unsigned um = (unsigned)m, lblk = um * R;
     const bool twiddled = m > 1;
+    const bool pad = PAD && pad_span > 0;
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> lgc;
         const unsigned blk = magic ? __umulhi(bi, magic) : bi;
         const unsigned j = bi - blk * um;
-        float2* xb = x + (((blk * lblk + j) << lgc) + col);
-        const unsigned st = um << lgc;
+        unsigned base = blk * lblk + j;
+        unsigned st = um << lgc;
+        if (pad) {   // the butterfly lies inside one span-S block (stage 0: one element per block)
+            base += __umulhi(base, pad_magic);
+            if (um == (unsigned)pad_span) st = um + 1;
+        }
+        float2* xb = x + ((base << lgc) + col);
         float2 v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = xb[t * st];
@@ -314,10 +322,11 @@ __device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, in
 }
 
 // The inverse of dif_stage (up to the factor R): inputs times conj(w_(R m)^(j q)), inverse DFT.
-template <class B, int LGC>
+template <class B, int LGC, bool PAD>
 __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt, int Lw, int m,
                                               unsigned magic, int tw_step,
-                                              const float2* __restrict__ tw)
+                                              const float2* __restrict__ tw, int pad_span,
+                                              unsigned pad_magic)
 {
     constexpr int R = B::R;
     const int lgc = LGC >= 0 ? LGC : lgc_rt;
@@ -325,13 +334,19 @@ __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt
     const unsigned total = (unsigned)(Lw / R) << lgc;
     const unsigned um = (unsigned)m, lblk = um * R;
     const bool twiddled = m > 1;
+    const bool pad = PAD && pad_span > 0;
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> lgc;
         const unsigned blk = magic ? __umulhi(bi, magic) : bi;
         const unsigned j = bi - blk * um;
-        float2* xb = x + (((blk * lblk + j) << lgc) + col);
-        const unsigned st = um << lgc;
+        unsigned base = blk * lblk + j;
+        unsigned st = um << lgc;
+        if (pad) {   // the butterfly lies inside one span-S block (stage 0: one element per block)
+            base += __umulhi(base, pad_magic);
+            if (um == (unsigned)pad_span) st = um + 1;
+        }
+        float2* xb = x + ((base << lgc) + col);
         float2 v[R];
         if (twiddled) {
             float2 w[R];
@@ -351,7 +366,7 @@ __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt
     }
 }
 
-template <int LGC>
+template <int LGC, bool PAD>
 __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlanDev& p,
                                                const float2* tw)
 {
@@ -361,21 +376,21 @@ __device__ __forceinline__ void direct_forward(float2* x, int lgc, const FftPlan
         const unsigned mg = p.magic[s];
         const int tw_step = Lw / (m * R);
         switch (R) {
-            case 16: dif_stage<OneLevel<16>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 15: dif_stage<TwoLevel<3, 5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 9: dif_stage<TwoLevel<3, 3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 8: dif_stage<OneLevel<8>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 4: dif_stage<OneLevel<4>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 2: dif_stage<OneLevel<2>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 3: dif_stage<OneLevel<3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 5: dif_stage<OneLevel<5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            default: dif_stage<OneLevel<7>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 16: dif_stage<OneLevel<16>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 15: dif_stage<TwoLevel<3, 5>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 9: dif_stage<TwoLevel<3, 3>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 8: dif_stage<OneLevel<8>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 4: dif_stage<OneLevel<4>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 2: dif_stage<OneLevel<2>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 3: dif_stage<OneLevel<3>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 5: dif_stage<OneLevel<5>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            default: dif_stage<OneLevel<7>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
         }
         __syncthreads();
     }
 }
 
-template <int LGC>
+template <int LGC, bool PAD>
 __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlanDev& p,
                                                const float2* tw)
 {
@@ -385,15 +400,15 @@ __device__ __forceinline__ void direct_inverse(float2* x, int lgc, const FftPlan
         const unsigned mg = p.magic[s];
         const int tw_step = Lw / (m * R);
         switch (R) {
-            case 16: dit_inv_stage<OneLevel<16>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 15: dit_inv_stage<TwoLevel<3, 5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 9: dit_inv_stage<TwoLevel<3, 3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 8: dit_inv_stage<OneLevel<8>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 4: dit_inv_stage<OneLevel<4>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 2: dit_inv_stage<OneLevel<2>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 3: dit_inv_stage<OneLevel<3>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            case 5: dit_inv_stage<OneLevel<5>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
-            default: dit_inv_stage<OneLevel<7>, LGC>(x, lgc, Lw, m, mg, tw_step, tw); break;
+            case 16: dit_inv_stage<OneLevel<16>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 15: dit_inv_stage<TwoLevel<3, 5>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 9: dit_inv_stage<TwoLevel<3, 3>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 8: dit_inv_stage<OneLevel<8>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 4: dit_inv_stage<OneLevel<4>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 2: dit_inv_stage<OneLevel<2>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 3: dit_inv_stage<OneLevel<3>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            case 5: dit_inv_stage<OneLevel<5>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
+            default: dit_inv_stage<OneLevel<7>, LGC, PAD>(x, lgc, Lw, m, mg, tw_step, tw, p.pad_span, p.pad_magic); break;
         }
         __syncthreads();
     }
@@ -418,11 +433,11 @@ __device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& 
         x[i] = v;
     }
     __syncthreads();
-    direct_forward<LGC>(x, lgc, p, tw);
+    direct_forward<LGC, false>(x, lgc, p, tw);
     for (int i = threadIdx.x; i < (Lw << lgc); i += blockDim.x)
         x[i] = cmul(x[i], __ldg(p.bhat + (i >> lgc)));
     __syncthreads();
-    direct_inverse<LGC>(x, lgc, p, tw);
+    direct_inverse<LGC, false>(x, lgc, p, tw);
     for (int i = threadIdx.x; i < (N << lgc); i += blockDim.x) {
         const float2 v = cmul(x[i], __ldg(p.chirp + (i >> lgc)));
         x[i] = INV ? cconj(v) : v;
@@ -431,22 +446,29 @@ __device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& 
 }
 
 // Forward DFT of every column: natural input; frequency k ends at position perm[k].
-// LGC >= 0 fixes lgc at compile time (rows: 0); LGC = -1 reads it at run time.
-template <int LGC = -1>
+// LGC >= 0 fixes lgc at compile time (rows: 0); LGC = -1 reads it at run time.  PAD: x is a
+// padded row buffer (Bluestein plans have no padding).
+template <int LGC = -1, bool PAD = false>
 __device__ __forceinline__ void fft_forward(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
     if (p.bluestein) bluestein<false, LGC>(x, lgc, p, tw);
-    else direct_forward<LGC>(x, lgc, p, tw);
+    else direct_forward<LGC, PAD>(x, lgc, p, tw);
 }
 
 // Unnormalised inverse DFT: frequency k read from position perm[k]; natural output.
-template <int LGC = -1>
+template <int LGC = -1, bool PAD = false>
 __device__ __forceinline__ void fft_inverse(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
     if (p.bluestein) bluestein<true, LGC>(x, lgc, p, tw);
-    else direct_inverse<LGC>(x, lgc, p, tw);
+    else direct_inverse<LGC, PAD>(x, lgc, p, tw);
+}
+
+// Buffer index of work position q in a padded row buffer.
+__device__ __forceinline__ unsigned row_pos(const FftPlanDev& p, unsigned q)
+{
+    return p.pad_span ? q + __umulhi(q, p.pad_magic) : q;
 }
 
 }  // namespace blfls

@@ -74,6 +74,21 @@ bool factor_direct(int N, std::vector<int>& radices)
     return n == 1 && int(radices.size()) <= kMaxStages;
 }
 
+// Row-buffer padding (see FftPlanDev::pad_span), with its multiply-high checked for every p < L.
+static bool fill_padding(FftPlanDev& d)
+{
+    d.pad_span = 0;
+    d.pad_magic = 0;
+    if (d.bluestein || d.nst < 2) return true;
+    const unsigned S = (unsigned)(d.L / d.radix[0]);
+    const unsigned magic = (unsigned)((((unsigned long long)1 << 32) + S - 1) / S);
+    for (unsigned q = 0; q < (unsigned)d.L; ++q)
+        if ((unsigned)(((unsigned long long)q * magic) >> 32) != q / S) return false;
+    d.pad_span = (int)S;
+    d.pad_magic = magic;
+    return true;
+}
+
 bool fill_stage_division(FftPlanDev& d)
 {
     int span = d.L;
@@ -110,7 +125,7 @@ cudaError_t build_fft_plan(int N, FftPlanHost& out)
     d.bluestein = direct ? 0 : 1;
     d.nst = int(radices.size());
     for (int s = 0; s < d.nst; ++s) d.radix[s] = radices[s];
-    if (!fill_stage_division(d)) return cudaErrorInvalidValue;
+    if (!fill_stage_division(d) || !fill_padding(d)) return cudaErrorInvalidValue;
 
     // Host tables.
     std::vector<float2> tw(L);
@@ -218,7 +233,7 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     rel.bluestein = direct ? 0 : 1;
     rel.nst = int(radices.size());
     for (int s = 0; s < rel.nst; ++s) rel.radix[s] = radices[s];
-    if (!fill_stage_division(rel)) return false;
+    if (!fill_stage_division(rel) || !fill_padding(rel)) return false;
 
     std::vector<float2> tw(L);
     for (int m = 0; m < L; ++m) {

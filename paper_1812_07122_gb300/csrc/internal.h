@@ -36,7 +36,18 @@ struct FftPlanDev {
     const float2* bhat;    // L entries (Bluestein): DFT_L of the conjugate chirp / L, in the
                            // direct transform's position order
     const float* lap;      // N entries: 4 sin^2(pi k / N), the periodic Laplacian's eigenvalues
+    // Row buffers place work position p at p + p / S, S = pad_span = L / radix[0] (direct plans
+    // of two or more stages; 0 = no padding), so that positions S apart (the digit-reversed
+    // neighbours k, k+1) fall in different shared-memory banks.
+    int pad_span;
+    unsigned pad_magic;    // ceil(2^32 / S): p / S = umulhi(p, pad_magic) for every p < L
 };
+
+// Elements of a padded row buffer for plan p.
+__host__ __device__ inline int row_buf_elems(const FftPlanDev& p)
+{
+    return p.L + (p.pad_span ? p.L / p.pad_span : 0);
+}
 
 struct FftPlanHost {
     FftPlanDev dev{};

@@ -45,7 +45,7 @@ __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const F
 // packed as z = r0 + i r1 into `data`.  Ends synchronised, so the rows may be overwritten after.
 __device__ __forceinline__ void k2_build(const float* ex0, const float* ex1, const float* eym,
                                          const float* ey0, const float* ey1, bool has1, int W,
-                                         float2* data)
+                                         const FftPlanDev& rp, float2* data)
 {
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int xm = (x == 0) ? W - 1 : x - 1;
@@ -53,7 +53,7 @@ __device__ __forceinline__ void k2_build(const float* ex0, const float* ex1, con
         const float r0 = (ex0[xm] - ex0[x]) + (eym[x] - ey0[x]);
         float r1 = 0.f;
         if (has1) r1 = (ex1[xm] - ex1[x]) + (ey0[x] - ey1[x]);
-        data[x] = make_float2(r0, r1);
+        data[row_pos(rp, x)] = make_float2(r0, r1);
     }
     __syncthreads();
 }
@@ -63,11 +63,11 @@ __device__ __forceinline__ void k2_transform(bool has1, int W, float2* s0, float
                                              const FftPlanDev& rp, const float2* tw, float2* data)
 {
     const int Wh = W / 2 + 1;
-    fft_forward<0>(data, 0, rp, tw);
+    fft_forward<0, true>(data, 0, rp, tw);
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
-        const float2 zk = data[__ldg(rp.perm + k)];
-        const float2 zn = data[__ldg(rp.perm + kn)];
+        const float2 zk = data[row_pos(rp, __ldg(rp.perm + k))];
+        const float2 zn = data[row_pos(rp, __ldg(rp.perm + kn))];
         // A = (Z_k + conj Z_{W-k}) / 2,  B = (Z_k - conj Z_{W-k}) / (2i)
         s0[k] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
         if (has1) s1[k] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
@@ -81,7 +81,7 @@ __device__ __forceinline__ void k2_rows(const float* ex0, const float* ex1, cons
                                         float2* s0, float2* s1, const FftPlanDev& rp,
                                         const float2* tw, float2* data)
 {
-    k2_build(ex0, ex1, eym, ey0, ey1, has1, W, data);
+    k2_build(ex0, ex1, eym, ey0, ey1, has1, W, rp, data);
     k2_transform(has1, W, s0, s1, rp, tw, data);
 }
 
@@ -164,17 +164,18 @@ __device__ __forceinline__ void k4_rebuild(const float2* s0, const float2* s1, b
         if (upper) { a.y = -a.y; b.y = -b.y; }
         if (k == 0 || 2 * k == W) { a.y = 0.f; b.y = 0.f; }  // real bins of a real row
         // Z = A + i B
-        data[__ldg(rp.perm + k)] = make_float2(a.x - b.y, a.y + b.x);
+        data[row_pos(rp, __ldg(rp.perm + k))] = make_float2(a.x - b.y, a.y + b.x);
     }
     __syncthreads();
 }
 
 // K4, last step (after the inverse FFT): u = f + result, real part row a, imaginary part row b.
 __device__ __forceinline__ void k4_output(bool has1, const float* f0, const float* f1, float* o0,
-                                          float* o1, int W, const float2* data)
+                                          float* o1, int W, const FftPlanDev& rp,
+                                          const float2* data)
 {
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const float2 z = data[x];
+        const float2 z = data[row_pos(rp, x)];
         o0[x] = f0[x] + z.x;
         if (has1) o1[x] = f1[x] + z.y;
     }
@@ -188,8 +189,8 @@ __device__ __forceinline__ void k4_rows(const float2* s0, const float2* s1, bool
                                         float2* data)
 {
     k4_rebuild(s0, s1, has1, W, rp, data);
-    fft_inverse<0>(data, 0, rp, tw);
-    k4_output(has1, f0, f1, o0, o1, W, data);
+    fft_inverse<0, true>(data, 0, rp, tw);
+    k4_output(has1, f0, f1, o0, o1, W, rp, data);
 }
 
 // K4: row pair `pair` of one channel, read from global memory.
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(512) k2_rows_forward(
     int H, int W, FftPlanDev rp, int tw_in_smem)
 {
     extern __shared__ float2 smem[];
-    const float2* tw = stage_twiddles(smem + rp.L, rp, tw_in_smem);
+    const float2* tw = stage_twiddles(smem + row_buf_elems(rp), rp, tw_in_smem);
     const int npairs = (H + 1) / 2;
     for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x)
         k2_item(ex, ey, spec, H, W, pair, rp, tw, smem);
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(512) k4_rows_inverse(
     int tw_in_smem)
 {
     extern __shared__ float2 smem[];
-    const float2* tw = stage_twiddles(smem + rp.L, rp, tw_in_smem);
+    const float2* tw = stage_twiddles(smem + row_buf_elems(rp), rp, tw_in_smem);
     const int npairs = (H + 1) / 2;
     for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x)
         k4_item(spec, f, out, H, W, pair, rp, tw, smem);
@@ -298,15 +299,15 @@ constexpr int kStagedThreads = 256;
 __host__ __device__ __forceinline__ size_t row_floats(int W) { return (size_t)((W + 3) & ~3); }
 // K2: [5][Wp] floats (e_x rows y0, y1; e_y rows y0-1, y0, y1), then the FFT buffer.
 __host__ __device__ __forceinline__ size_t k2s_stage_bytes(int W) { return sizeof(float) * 5 * row_floats(W); }
-__host__ __device__ __forceinline__ size_t k2s_smem(int W, int L)
+__host__ __device__ __forceinline__ size_t k2s_smem(int W, const FftPlanDev& rp)
 {
-    return k2s_stage_bytes(W) + sizeof(float2) * (size_t)L;
+    return k2s_stage_bytes(W) + sizeof(float2) * (size_t)row_buf_elems(rp);
 }
 // K4: [2][Wh] half spectra, [2][Wp] floats of f, then the FFT buffer.
 __host__ __device__ __forceinline__ size_t k4s_spec_bytes(int W) { return align16(sizeof(float2) * 2 * (size_t)(W / 2 + 1)); }
-__host__ __device__ __forceinline__ size_t k4s_smem(int W, int L)
+__host__ __device__ __forceinline__ size_t k4s_smem(int W, const FftPlanDev& rp)
 {
-    return k4s_spec_bytes(W) + sizeof(float) * 2 * row_floats(W) + sizeof(float2) * (size_t)L;
+    return k4s_spec_bytes(W) + sizeof(float) * 2 * row_floats(W) + sizeof(float2) * (size_t)row_buf_elems(rp);
 }
 // K3: two column blocks (double-buffered; the FFT runs in place in one of them), then the
 // plan's twiddle table.
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float*
         __syncthreads();
         const int y0 = 2 * p, y1 = y0 + 1;
         const bool has1 = y1 < H;
-        k2_build(st, st + Wp, st + 2 * Wp, st + 3 * Wp, st + 4 * Wp, has1, W, data);
+        k2_build(st, st + Wp, st + 2 * Wp, st + 3 * Wp, st + 4 * Wp, has1, W, rp, data);
         if (p + 1 < p1) issue(p + 1);   // the rows of pair p have been read out
         k2_transform(has1, W, spec + (size_t)y0 * Wh, spec + (size_t)(has1 ? y1 : y0) * Wh, rp,
                      rp.tw, data);
@@ -393,11 +394,11 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
         k4_rebuild(ss, ss + Wh, has1, W, rp, data);
         const bool more = p + 1 < p1;
         if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
-        fft_inverse<0>(data, 0, rp, rp.tw);
+        fft_inverse<0, true>(data, 0, rp, rp.tw);
         if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
         __syncthreads();
         k4_output(has1, sf, sf + Wp, out + (size_t)y0 * W, out + (size_t)(has1 ? y1 : y0) * W, W,
-                  data);
+                  rp, data);
         if (more) issue_f(p + 1);
     }
 }
@@ -542,7 +543,7 @@ void init_solve_kernel_attributes()
 
 size_t solve_smem_rows(const FftPlanDev& rp)
 {
-    const size_t data = sizeof(float2) * rp.L;
+    const size_t data = sizeof(float2) * row_buf_elems(rp);
     const size_t tw = sizeof(float2) * rp.L;
     return data + tw <= kSmemCap ? data + tw : data;
 }
@@ -611,7 +612,7 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     const size_t cap = kSmemCap;
     const bool al16 = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(ex) | reinterpret_cast<uintptr_t>(ey) |
                                         reinterpret_cast<uintptr_t>(f)) % 16 == 0);
-    const bool rows_staged = k2s_smem(W, rp.L) <= cap && k4s_smem(W, rp.L) <= cap;
+    const bool rows_staged = k2s_smem(W, rp) <= cap && k4s_smem(W, rp) <= cap;
     int lgc = solve_fit_lgc(cp.L, p.col_block);
     while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
     const bool cols_staged = k3s_smem(cp.L, lgc) <= cap;
@@ -620,14 +621,14 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     const int nblk = (W / 2 + 1 + CB - 1) / CB;
 
     if (rows_staged) {
-        const size_t sm2 = k2s_smem(W, rp.L);
+        const size_t sm2 = k2s_smem(W, rp);
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_staged, kStagedThreads, sm2);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
         k2_rows_staged<<<grid, kStagedThreads, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
-        const int tw_r = smem_r > sizeof(float2) * rp.L;
+        const int tw_r = smem_r > sizeof(float2) * row_buf_elems(rp);
         const int thr_r = threads_for(rp.L / 4);
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_forward, thr_r, smem_r);
@@ -655,14 +656,14 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     }
     if (marks) cudaEventRecord(marks[1], s);
     if (rows_staged) {
-        const size_t sm4 = k4s_smem(W, rp.L);
+        const size_t sm4 = k4s_smem(W, rp);
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_staged, kStagedThreads, sm4);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
         k4_rows_staged<<<grid, kStagedThreads, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
-        const int tw_r = smem_r > sizeof(float2) * rp.L;
+        const int tw_r = smem_r > sizeof(float2) * row_buf_elems(rp);
         const int thr_r = threads_for(rp.L / 4);
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_inverse, thr_r, smem_r);
