@@ -64,6 +64,7 @@ __device__ __forceinline__ void k2_transform(bool has1, int W, float2* s0, float
 {
     const int Wh = W / 2 + 1;
     fft_forward<0, true>(data, 0, rp, tw);
+#pragma unroll 4
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
         const float2 zk = data[row_pos(rp, __ldg(rp.perm + k))];
@@ -104,10 +105,12 @@ __device__ __forceinline__ void k2_item(const float* __restrict__ ex, const floa
 // down the columns, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the 1/(HW) of the
 // inverse), inverse FFT.  Ends synchronised.
 template <int LGC = -1>
+// `syp`, when given, holds sy[iperm[p]] for every work position p (staged once per CTA).
 __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int kx0, int lgc,
                                                const FftPlanDev& cp, const float* __restrict__ sx,
                                                const float* __restrict__ sy, float lam,
-                                               float scale, const float2* tw)
+                                               float scale, const float2* tw,
+                                               const float* syp = nullptr)
 {
     const int CB = 1 << lgc;
     const int Wh = W / 2 + 1;
@@ -117,8 +120,8 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
     for (int i = threadIdx.x; i < (nfreq << lgc); i += blockDim.x) {
         const int p = i >> lgc, c = i & (CB - 1);
         const int kx = min(kx0 + c, Wh - 1);
-        const int ky = __ldg(cp.iperm + p);
-        const float den = fmaf(lam, __ldg(sx + kx) + __ldg(sy + ky), 1.0f);
+        const float syv = syp ? syp[p] : __ldg(sy + __ldg(cp.iperm + p));
+        const float den = fmaf(lam, __ldg(sx + kx) + syv, 1.0f);
         const float m = __fdividef(scale, den) * lam;
         const float2 v = data[i];
         data[i] = make_float2(v.x * m, v.y * m);
@@ -156,6 +159,7 @@ __device__ __forceinline__ void k3_item(float2* __restrict__ spec, int H, int W,
 __device__ __forceinline__ void k4_rebuild(const float2* s0, const float2* s1, bool has1, int W,
                                            const FftPlanDev& rp, float2* data)
 {
+#pragma unroll 4
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
         const bool upper = k > W / 2;
         const int kk = upper ? W - k : k;
@@ -240,9 +244,23 @@ __device__ __forceinline__ void stage_floats(float* dst, const float* src, int n
         for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(dst + i, src + i);
     }
 }
+// Stage n complex values: 16-byte copies (which bypass L1) when src and dst share their
+// alignment modulo 16 bytes, with at most one 8-byte copy at either end; else 8-byte copies.
 __device__ __forceinline__ void stage_complex(float2* dst, const float2* src, int n)
 {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async8(dst + i, src + i);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src), d = reinterpret_cast<uintptr_t>(dst);
+    if (((a ^ d) & 15) != 0) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async8(dst + i, src + i);
+        return;
+    }
+    const int lead = (a & 15) ? 1 : 0;
+    const int npairs = (n - lead) >> 1;
+    if (threadIdx.x == 0) {
+        if (lead && n > 0) cp_async8(dst, src);
+        if (((n - lead) & 1) && n > lead) cp_async8(dst + n - 1, src + n - 1);
+    }
+    for (int i = threadIdx.x; i < npairs; i += blockDim.x)
+        cp_async16(dst + lead + 2 * i, src + lead + 2 * i);
 }
 
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -309,11 +327,12 @@ __host__ __device__ __forceinline__ size_t k4s_smem(int W, const FftPlanDev& rp)
 {
     return k4s_spec_bytes(W) + sizeof(float) * 2 * row_floats(W) + sizeof(float2) * (size_t)row_buf_elems(rp);
 }
-// K3: two column blocks (double-buffered; the FFT runs in place in one of them), then the
-// plan's twiddle table.
+// K3: two column blocks (double-buffered; the FFT runs in place in one of them), the plan's
+// twiddle table, and the column eigenvalues in work-position order (sy[iperm[p]]).
 __host__ __device__ __forceinline__ size_t k3s_smem(int L, int lgc)
 {
-    return 2 * (sizeof(float2) * (size_t)L << lgc) + sizeof(float2) * (size_t)L;
+    return 2 * (sizeof(float2) * (size_t)L << lgc) + sizeof(float2) * (size_t)L +
+           sizeof(float) * (size_t)L;
 }
 
 __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float* __restrict__ ex,
@@ -420,6 +439,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restr
     const size_t blk_elems = (size_t)cp.L << lgc;
     float2* bufs = reinterpret_cast<float2*>(staged_smem);
     float2* tws = bufs + 2 * blk_elems;
+    float* syp = reinterpret_cast<float*>(tws + cp.L);
     const int nblk = (Wh + CB - 1) >> lgc;
     int b0, b1;
     band(nblk, b0, b1);
@@ -435,7 +455,10 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restr
     };
     issue(b0, bufs);
     cp_commit();
-    for (int i = threadIdx.x; i < cp.L; i += blockDim.x) tws[i] = __ldg(cp.tw + i);
+    for (int i = threadIdx.x; i < cp.L; i += blockDim.x) {
+        tws[i] = __ldg(cp.tw + i);
+        syp[i] = __ldg(sy + __ldg(cp.iperm + i) % H);   // positions >= H (Bluestein scratch) unused
+    }
     for (int b = b0; b < b1; ++b) {
         float2* data = bufs + ((b - b0) & 1) * blk_elems;
         if (b + 1 < b1) {
@@ -447,7 +470,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restr
         }
         __syncthreads();
         const int kx0 = b * CB;
-        k3_solve_block<LGC>(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tws);
+        k3_solve_block<LGC>(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tws, syp);
         for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
             const int n = i >> lgc, c = i & (CB - 1);
             const int kx = kx0 + c;
