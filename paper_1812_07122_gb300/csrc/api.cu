@@ -221,6 +221,21 @@ static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex
     return e;
 }
 
+// The passes of one channel (the channels of an image are filtered and solved independently).
+static int run_channel(blfls_handle* h, const float* img, float* out, const BlfParams& bp,
+                       const SolveParams& sp, const FftPlanDev& rp, const FftPlanDev& cp,
+                       int iters, cudaStream_t s)
+{
+    for (int it = 0; it < iters; ++it) {
+        const float* src = (it == 0) ? img : out;
+        cudaError_t e = blf_launch(h, src, h->ex, h->ey, 1, bp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
+        e = solve_launch(h, src, h->ex, h->ey, out, rp, cp, sp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+    }
+    return BLFLS_OK;
+}
+
 int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
                       float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
                       cudaStream_t s)
@@ -239,15 +254,67 @@ int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int 
     if (rc != BLFLS_OK) return rc;
     const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
     const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
-    for (int it = 0; it < iters; ++it) {
-        const float* src = (it == 0) ? img : out;
-        for (int c = 0; c < C; ++c) {
-            cudaError_t e = blf_launch(h, src + c * plane, h->ex, h->ey, 1, bp, s);
-            if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
-            e = solve_launch(h, src + c * plane, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
-            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+    for (int c = 0; c < C; ++c)
+        if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
+            return rc;
+    return BLFLS_OK;
+}
+
+// blfls_smooth_host: channel c is computed on the caller's stream while the copy stream uploads
+// the channels after it and downloads the channels before it.
+static int smooth_host_pipelined(blfls_handle* h, const float* img_host, float* out_host, int H,
+                                 int W, int C, float lambda, float sigma_s, float sigma_r,
+                                 int radius, int iters, int prec, cudaStream_t s)
+{
+    const size_t plane = (size_t)H * W;
+    const size_t n = plane * C;
+    int rc;
+    if ((rc = grow(h, h->io, h->io_cap, 2 * n, "host-buffer staging")) != BLFLS_OK) return rc;
+    float* dimg = h->io;
+    float* dout = h->io + n;
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare(h, H, W, radius, true, true, &rp, &cp)) != BLFLS_OK) return rc;
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_stream) {
+        e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            h->copy_stream = nullptr;
+            return cuda_fail(e, "copy stream");
         }
     }
+    while ((int)h->io_events.size() < 2 * C + 1) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "copy events");
+        h->io_events.push_back(ev);
+    }
+    cudaStream_t cs = h->copy_stream;
+    cudaEvent_t* ev_in = h->io_events.data();
+    cudaEvent_t* ev_done = ev_in + C;
+    cudaEvent_t ev_fin = ev_in[2 * C];
+    // The copy stream starts after whatever the caller queued on s before this call.
+    if ((e = cudaEventRecord(ev_fin, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_fin, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
+    for (int c = 0; c < C; ++c) {
+        e = cudaMemcpyAsync(dimg + c * plane, img_host + c * plane, plane * sizeof(float),
+                            cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        if ((e = cudaEventRecord(ev_in[c], cs)) != cudaSuccess) return cuda_fail(e, "event record");
+    }
+    for (int c = 0; c < C; ++c) {
+        if ((e = cudaStreamWaitEvent(s, ev_in[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+        if ((rc = run_channel(h, dimg + c * plane, dout + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
+            return rc;
+        if ((e = cudaEventRecord(ev_done[c], s)) != cudaSuccess) return cuda_fail(e, "event record");
+        if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+        e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
+                            cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    if ((e = cudaEventRecord(ev_fin, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev_fin, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
     return BLFLS_OK;
 }
 
@@ -290,6 +357,8 @@ void blfls_destroy(blfls_handle* h)
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
     for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->io_events) cudaEventDestroy(ev);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     destroy_batch_state(h->batch);
     for (auto& kv : h->plans) free_fft_plan(kv.second);
     if (h->ex) cudaFree(h->ex);
@@ -333,18 +402,18 @@ int blfls_smooth_host(blfls_handle* h, const float* img_host, float* out_host, i
     if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
-    const size_t n = (size_t)H * W * C;
-    if ((rc = grow(h, h->io, h->io_cap, 2 * n, "host-buffer staging")) != BLFLS_OK) return rc;
-    float* dimg = h->io;
-    float* dout = h->io + n;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(dimg, img_host, n * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-    rc = run_smooth(h, dimg, dout, H, W, C, lambda, sigma_s, sigma_r, radius, iters, prec, s);
-    if (rc != BLFLS_OK) return rc;
-    e = cudaMemcpyAsync(out_host, dout, n * sizeof(float), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    e = cudaStreamSynchronize(s);
+    if (iters > 0) {
+        rc = smooth_host_pipelined(h, img_host, out_host, H, W, C, lambda, sigma_s, sigma_r, radius,
+                                   iters, prec, s);
+        if (rc != BLFLS_OK) return rc;
+    } else if (out_host != img_host) {
+        const size_t n = (size_t)H * W * C;
+        const cudaError_t e = cudaMemcpyAsync(out_host, img_host, n * sizeof(float),
+                                              cudaMemcpyHostToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy for iters = 0");
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     return BLFLS_OK;
 }

@@ -31,6 +31,9 @@ struct blfls_handle {
     size_t g_cap = 0;
     float* io = nullptr;  // device copies for blfls_smooth_host: img then out
     size_t io_cap = 0;
+    // blfls_smooth_host: copy stream (non-blocking) and per-channel events
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> io_events;
     // kernel timing (blfls_profile_begin / _end)
     bool prof_on = false;
     bool prof_overflow = false;

@@ -137,6 +137,24 @@ def test_host_entry_point_equals_device_entry_point(h):
     assert np.array_equal(dst.numpy(), dev)
 
 
+def test_host_entry_point_in_place_pageable_and_zero_iters(h):
+    """The host entry point overlaps per-channel copies with compute on its own copy stream;
+    in-place buffers, pageable memory and iters = 0 must give the device entry point's result."""
+    import torch
+    f = _img(48, 72, 3, seed=6)
+    dev = smooth(h, f, 30.0, 3.0, 0.1, 4, 2)
+    buf = torch.from_numpy(f.copy()).pin_memory()
+    blfls.blfls_smooth_host(h, buf, buf, 48, 72, 3, 30.0, 3.0, 0.1, 4, 2)
+    assert np.array_equal(buf.numpy(), dev)
+    src = torch.from_numpy(f.copy())
+    dst = torch.zeros_like(src)
+    blfls.blfls_smooth_host(h, src, dst, 48, 72, 3, 30.0, 3.0, 0.1, 4, 2)
+    assert np.array_equal(dst.numpy(), dev)
+    dst.zero_()
+    blfls.blfls_smooth_host(h, src, dst, 48, 72, 3, 30.0, 3.0, 0.1, 4, 0)
+    assert np.array_equal(dst.numpy(), f)
+
+
 def test_mean_is_preserved_on_gpu(h):
     f = _img(128, 96, 1, seed=3)
     u = smooth(h, f, 30.0, 3.0, 0.1, 5, 1)
