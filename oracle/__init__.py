@@ -15,3 +15,4 @@ from .blfls_ref import (  # noqa: F401
     gradients,
     solve_eq8,
 )
+from .layers_ref import detail_enhance, log_tone, ls, ls_channel  # noqa: F401
