@@ -14,7 +14,8 @@ Also reported: ``roofline`` for K1 (ALU-bound on the MUFU ex2 pipe; live per-lau
 events the library records around each launch), ``e2e`` (host buffers through
 ``blfls_smooth_host``, copies included), ``clocks`` sampled by nvidia-smi during the timed loop,
 ``cpu_baseline`` (the FP64 oracle on the host cores, bounded sample, rank 0 at N=1 only) and
-``forms`` (the FP16/BF16-weight precision forms on the same workload).
+``forms`` (the FP16/BF16-weight precision forms on the same workload), ``modes`` (the LS model of
+Eq. 6 and the detail-enhancement / log-tone applications of Section IV on the same image).
 
 ``--impl reference`` times the FP64 oracle instead (the comparison arm; no GPU work).
 """
@@ -51,6 +52,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the LS-model and base/detail lines")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -423,27 +426,46 @@ def main():
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "api": "blfls_smooth_host (pinned host buffers)"}
 
+    def timed_mp(fn, n):
+        """MP/s of fn() on the 4K workload: CUDA events around each call, L2 flushed between."""
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for i in range(n):
+            flush.fill_(float(i))
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return round(mp / (tot / n / 1e3), 2)
+
     # precision forms on the same workload
     forms = None
     if not args.no_forms:
         forms = {}
         for name, prec in [("fp32", 0), ("fp16w", 1), ("bf16w", 2)]:
             try:
-                step(prec)
-                torch.cuda.synchronize(dev)
-                n = max(3, K // 4)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                tot = 0.0
-                for i in range(n):
-                    flush.fill_(float(i))
-                    a.record(stream)
-                    step(prec)
-                    b.record(stream)
-                    b.synchronize()
-                    tot += a.elapsed_time(b)
-                forms[name] = round(mp / (tot / n / 1e3), 2)
+                forms[name] = timed_mp(lambda: step(prec), max(3, K // 4))
             except blfls.BlflsError as e:
                 forms[name] = f"unavailable: {e}"
+
+    # the LS model (Eq. 6) and the base/detail applications on the same image and parameters
+    modes = None
+    if not args.no_modes:
+        n = max(3, K // 4)
+        ls = lambda: blfls.blfls_smooth_ls(h, x, out, H, W, C, p["lam"], p["iters"], stream)
+        enh = lambda: blfls.blfls_layers(h, x, out, H, W, C, blfls.BLFLS_DETAIL_ENHANCE, 2.0,
+                                         p["lam"], p["sigma_s"], p["sigma_r"], p["radius"],
+                                         p["iters"], 0, stream)
+        tone = lambda: blfls.blfls_layers(h, x, out, H, W, C, blfls.BLFLS_LOG_TONE, 0.5,
+                                          p["lam"], p["sigma_s"], p["sigma_r"], p["radius"],
+                                          p["iters"], 0, stream)
+        modes = {"workload": "the same 4K RGB image and parameters, FP32",
+                 "ls_model": timed_mp(ls, n),
+                 "detail_enhance_m2": timed_mp(enh, n),
+                 "log_tone_c0.5": timed_mp(tone, n)}
 
     batched = None
     if not args.no_batch:
@@ -473,7 +495,7 @@ def main():
                            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * K, "clocks": clocks, "forms": forms,
-                "batched": batched, "serving": serving}
+                "modes": modes, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -103,6 +103,32 @@ int blfls_smooth_host(blfls_handle *h, const float *img_host, float *out_host, i
                       int C, float lambda, float sigma_s, float sigma_r, int radius, int iters,
                       int prec, void *stream);
 
+/* ---- The LS model and the base/detail applications ------------------------------------ */
+
+/* The LS model (Section II-B, Eqs. 5-6): u = F^-1[F(f) / (1 + lam (4 sin^2(pi kx / W) +
+ * 4 sin^2(pi ky / H)))], the un-weighted quadratic smoother (BLF-LS with the guidance
+ * gradients set to zero), applied `iters` times (0 copies).  Device pointers [C][H][W], async on
+ * `stream`; out may equal img.  Errors: BLFLS_EINVAL (as blfls_smooth), BLFLS_ENOMEM,
+ * BLFLS_ECUDA. */
+int blfls_smooth_ls(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                    float lambda, int iters, void *stream);
+
+typedef enum { BLFLS_DETAIL_ENHANCE = 0, BLFLS_LOG_TONE = 1 } blfls_layer_mode;
+#define BLFLS_LOG_FLOOR 1e-6f
+
+/* The base/detail applications of Section IV on top of the smoother (u = BLFLS^iters):
+ *   BLFLS_DETAIL_ENHANCE: u = BLFLS^iters(f); out = f + strength (f - u): the detail layer
+ *     f - u magnified by strength >= 0 and added back to the input;
+ *   BLFLS_LOG_TONE: l = ln(max(f, BLFLS_LOG_FLOOR)); b = BLFLS^iters(l);
+ *     out = exp(strength b + (l - b)): the base layer of the logarithmic image compressed by
+ *     strength in [0, 1], the detail layer kept (the caller rescales the result for display).
+ * Other arguments as blfls_smooth (iters >= 1); out may equal img; the handle keeps one
+ * [C][H][W] scratch image.  Errors: BLFLS_EINVAL (unknown mode, strength out of range or not
+ * finite, other arguments as blfls_smooth), BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_layers(blfls_handle *h, const float *img, float *out, int H, int W, int C, int mode,
+                 float strength, float lambda, float sigma_s, float sigma_r, int radius,
+                 int iters, int prec, void *stream);
+
 /* Step 1 alone (Eq. 1 on the gradients of Section II-B): for every channel,
  *   ex = f_BLF(D_x img) - D_x img,   ey = f_BLF(D_y img) - D_y img,
  * i.e. how far the bilateral filter moves each gradient field.  ex, ey: device [C][H][W]. */

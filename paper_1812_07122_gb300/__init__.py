@@ -8,17 +8,21 @@ and raises if it has not been built.
 from . import blfls  # noqa: F401
 from .blfls import (  # noqa: F401
     BLFLS_BF16W,
+    BLFLS_DETAIL_ENHANCE,
     BLFLS_FP16W,
     BLFLS_FP32,
+    BLFLS_LOG_TONE,
     BlflsError,
     Smoother,
     blfls_blf_residual,
     blfls_create,
     blfls_destroy,
     blfls_last_error,
+    blfls_layers,
     blfls_smooth,
     blfls_smooth_batch,
     blfls_smooth_host,
+    blfls_smooth_ls,
     blfls_solve_residual,
     make_job,
 )

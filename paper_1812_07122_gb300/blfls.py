@@ -25,6 +25,10 @@ BLFLS_FP32 = 0
 BLFLS_FP16W = 1
 BLFLS_BF16W = 2
 
+BLFLS_DETAIL_ENHANCE = 0
+BLFLS_LOG_TONE = 1
+BLFLS_LOG_FLOOR = 1e-6
+
 BLFLS_MAX_DIM = 8192
 BLFLS_MAX_CHANNELS = 4
 BLFLS_MAX_ITERS = 64
@@ -100,6 +104,9 @@ _SIGNATURES = {
     "blfls_solve_residual_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int,
                                               _c_float, _vp]),
     "blfls_profile_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
+    "blfls_smooth_ls": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp]),
+    "blfls_layers": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_float, _c_float,
+                              _c_float, _c_float, _c_int, _c_int, _c_int, _vp]),
 }
 
 
@@ -184,6 +191,21 @@ def blfls_smooth_host(h, img_host, out_host, H, W, C, lam, sigma_s, sigma_r, rad
     _check(load().blfls_smooth_host(h, _ptr(img_host), _ptr(out_host), int(H), int(W), int(C),
                                     float(lam), float(sigma_s), float(sigma_r), int(radius),
                                     int(iters), _prec(prec), _stream(stream)), h)
+
+
+def blfls_smooth_ls(h, img, out, H, W, C, lam, iters=1, stream=None) -> None:
+    """The LS model (Eqs. 5-6) on device buffers."""
+    _check(load().blfls_smooth_ls(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(lam),
+                                  int(iters), _stream(stream)), h)
+
+
+def blfls_layers(h, img, out, H, W, C, mode, strength, lam, sigma_s, sigma_r, radius, iters=1,
+                 prec=BLFLS_FP32, stream=None) -> None:
+    """Detail enhancement (mode BLFLS_DETAIL_ENHANCE) or log-domain tone mapping
+    (BLFLS_LOG_TONE) on top of the smoother, device buffers."""
+    _check(load().blfls_layers(h, _ptr(img), _ptr(out), int(H), int(W), int(C), int(mode),
+                               float(strength), float(lam), float(sigma_s), float(sigma_r),
+                               int(radius), int(iters), _prec(prec), _stream(stream)), h)
 
 
 def blfls_blf_residual(h, img, ex, ey, H, W, C, sigma_s, sigma_r, radius, prec=BLFLS_FP32,

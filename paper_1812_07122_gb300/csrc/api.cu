@@ -365,6 +365,7 @@ void blfls_destroy(blfls_handle* h)
     if (h->spec) cudaFree(h->spec);
     if (h->gscratch) cudaFree(h->gscratch);
     if (h->io) cudaFree(h->io);
+    if (h->layer) cudaFree(h->layer);
     delete h;
 }
 
@@ -416,6 +417,75 @@ int blfls_smooth_host(blfls_handle* h, const float* img_host, float* out_host, i
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     return BLFLS_OK;
+}
+
+int blfls_smooth_ls(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                    float lambda, int iters, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out == img) return BLFLS_OK;
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare(h, H, W, 0, false, true, &rp, &cp)) != BLFLS_OK) return rc;
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int c = 0; c < C; ++c)
+        for (int it = 0; it < iters; ++it) {
+            const float* src = (it == 0 ? img : out) + c * plane;
+            cudaError_t e = launch_ls_residuals(src, h->ex, h->ey, H, W, s, h->num_sms);
+            if (e != cudaSuccess) return cuda_fail(e, "LS residual kernel launch");
+            e = solve_launch(h, src, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+        }
+    return BLFLS_OK;
+}
+
+int blfls_layers(blfls_handle* h, const float* img, float* out, int H, int W, int C, int mode,
+                 float strength, float lambda, float sigma_s, float sigma_r, int radius,
+                 int iters, int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 1 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [1, BLFLS_MAX_ITERS]");
+    if (mode != BLFLS_DETAIL_ENHANCE && mode != BLFLS_LOG_TONE) return fail(BLFLS_EINVAL, "unknown layer mode");
+    if (!std::isfinite(strength) || strength < 0.f || (mode == BLFLS_LOG_TONE && strength > 1.f))
+        return fail(BLFLS_EINVAL, "strength must be finite, >= 0, and <= 1 for BLFLS_LOG_TONE");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)H * W * C;
+    if ((rc = grow(h, h->layer, h->layer_cap, n, "layer image")) != BLFLS_OK) return rc;
+    cudaError_t e;
+    if (mode == BLFLS_DETAIL_ENHANCE) {
+        // u into the scratch image, then out = f + m (f - u)
+        if ((rc = run_smooth(h, img, h->layer, H, W, C, lambda, sigma_s, sigma_r, radius, iters,
+                             prec, s)) != BLFLS_OK)
+            return rc;
+        e = launch_layer_epilogue(0, img, h->layer, out, n, strength, s, h->num_sms);
+    } else {
+        // l into the scratch image, b = BLFLS(l) into out, then out = exp(c b + (l - b))
+        e = launch_log_image(img, h->layer, n, BLFLS_LOG_FLOOR, s, h->num_sms);
+        if (e != cudaSuccess) return cuda_fail(e, "log kernel launch");
+        if ((rc = run_smooth(h, h->layer, out, H, W, C, lambda, sigma_s, sigma_r, radius, iters,
+                             prec, s)) != BLFLS_OK)
+            return rc;
+        e = launch_layer_epilogue(1, h->layer, out, out, n, strength, s, h->num_sms);
+    }
+    return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "layer epilogue launch");
 }
 
 int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, int H, int W,

@@ -31,6 +31,8 @@ struct blfls_handle {
     size_t g_cap = 0;
     float* io = nullptr;  // device copies for blfls_smooth_host: img then out
     size_t io_cap = 0;
+    float* layer = nullptr;  // blfls_layers: the smoothed (or logarithmic) image
+    size_t layer_cap = 0;
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;

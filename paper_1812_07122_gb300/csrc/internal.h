@@ -146,4 +146,12 @@ cudaError_t launch_solve_batch(const BatchJob* jobs, int njobs, const int2* grp_
                                size_t smem_rows, size_t smem_cols, int num_sms, cudaStream_t s,
                                const cudaEvent_t* marks = nullptr);
 
+// Elementwise kernels of the LS model and of the base/detail applications (layers.cu).
+cudaError_t launch_ls_residuals(const float* f, float* ex, float* ey, int H, int W,
+                                cudaStream_t s, int num_sms);
+cudaError_t launch_log_image(const float* f, float* l, size_t n, float floor_v, cudaStream_t s,
+                             int num_sms);
+cudaError_t launch_layer_epilogue(int mode, const float* f, const float* u, float* out, size_t n,
+                                  float strength, cudaStream_t s, int num_sms);
+
 }  // namespace blfls
