@@ -16,3 +16,10 @@ from .blfls_ref import (  # noqa: F401
     solve_eq8,
 )
 from .layers_ref import detail_enhance, log_tone, ls, ls_channel  # noqa: F401
+from .guided_ref import (  # noqa: F401
+    blf_joint,
+    blfls_joint,
+    blfls_rolling,
+    gaussian,
+    gaussian_weights,
+)
