@@ -15,7 +15,8 @@ events the library records around each launch), ``e2e`` (host buffers through
 ``blfls_smooth_host``, copies included), ``clocks`` sampled by nvidia-smi during the timed loop,
 ``cpu_baseline`` (the FP64 oracle on the host cores, bounded sample, rank 0 at N=1 only) and
 ``forms`` (the FP16/BF16-weight precision forms on the same workload), ``modes`` (the LS model of
-Eq. 6 and the detail-enhancement / log-tone applications of Section IV on the same image).
+Eq. 6, the detail-enhancement / log-tone applications of Section IV, and joint and rolling-
+guidance smoothing of Section III-D on the same image).
 
 ``--impl reference`` times the FP64 oracle instead (the comparison arm; no GPU work).
 """
@@ -462,10 +463,21 @@ def main():
         tone = lambda: blfls.blfls_layers(h, x, out, H, W, C, blfls.BLFLS_LOG_TONE, 0.5,
                                           p["lam"], p["sigma_s"], p["sigma_r"], p["radius"],
                                           p["iters"], 0, stream)
+        guide = torch.empty_like(x)
+        blfls.blfls_gaussian(h, x, guide, H, W, C, 2.0, stream)   # a smooth guidance image
+        out2 = torch.empty_like(x)
+        joint = lambda: blfls.blfls_smooth_guided(h, x, guide, out, H, W, C, C, p["lam"],
+                                                  p["sigma_s"], p["sigma_r"], p["radius"],
+                                                  p["iters"], 0, stream)
+        rolling = lambda: blfls.blfls_smooth_rolling(h, x, out2, H, W, C, p["lam"], p["sigma_s"],
+                                                     p["sigma_r"], p["radius"], p["iters"], 1.0,
+                                                     0, stream)
         modes = {"workload": "the same 4K RGB image and parameters, FP32",
                  "ls_model": timed_mp(ls, n),
                  "detail_enhance_m2": timed_mp(enh, n),
-                 "log_tone_c0.5": timed_mp(tone, n)}
+                 "log_tone_c0.5": timed_mp(tone, n),
+                 "joint_guided_by_gaussian2": timed_mp(joint, n),
+                 "rolling_guidance_sigma1": timed_mp(rolling, n)}
 
     batched = None
     if not args.no_batch:

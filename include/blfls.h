@@ -129,6 +129,39 @@ int blfls_layers(blfls_handle *h, const float *img, float *out, int H, int W, in
                  float strength, float lambda, float sigma_s, float sigma_r, int radius,
                  int iters, int prec, void *stream);
 
+/* ---- Joint (guided) BLF-LS and rolling guidance (Section III-D) -------------------------- */
+
+#define BLFLS_MAX_GAUSS_SIGMA 32.0f
+
+/* Joint BLF-LS: as blfls_smooth, but the range weights of the bilateral filter on each gradient
+ * field compare that field of the guidance image's gradients (guide: device [Cg][H][W],
+ * Cg = C, or Cg = 1 shared by every channel); the values averaged are the input's gradients,
+ * as in a joint bilateral filter.  Pass k > 1 smooths the previous output with the same
+ * guidance.  With sigma_r = +inf the guidance has no effect.  Radii up to
+ * BLFLS_MAX_HALF_RADIUS run the tiled kernels in every precision; larger radii (FP32 only) a
+ * per-pixel kernel.  out may equal img but not guide.  Errors: BLFLS_EINVAL (guide NULL, Cg
+ * not 1 or C, out == guide, other arguments as blfls_smooth), BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_smooth_guided(blfls_handle *h, const float *img, const float *guide, float *out, int H,
+                        int W, int C, int Cg, float lambda, float sigma_s, float sigma_r,
+                        int radius, int iters, int prec, void *stream);
+
+/* Rolling guidance: the first guidance is the input smoothed by the periodic Gaussian of
+ * standard deviation sigma_g (blfls_gaussian); pass k is joint BLF-LS of the INPUT guided by
+ * guidance k, and its output is guidance k + 1; out receives pass `iters` (iters = 0 copies).
+ * out must not equal img (every pass reads the input).  Errors: BLFLS_EINVAL (out == img,
+ * sigma_g outside (0, BLFLS_MAX_GAUSS_SIGMA], other arguments as blfls_smooth), BLFLS_ENOMEM,
+ * BLFLS_ECUDA. */
+int blfls_smooth_rolling(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                         float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                         float sigma_g, int prec, void *stream);
+
+/* Periodic Gaussian blur, rows then columns, taps exp(-x^2 / (2 sigma^2)) for
+ * |x| <= ceil(3 sigma) normalised to sum 1 (computed in FP64 on the host, stored FP32); device
+ * [C][H][W] buffers, async; out may equal img.  Errors: BLFLS_EINVAL (sigma outside
+ * (0, BLFLS_MAX_GAUSS_SIGMA], image arguments), BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_gaussian(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                   float sigma, void *stream);
+
 /* Step 1 alone (Eq. 1 on the gradients of Section II-B): for every channel,
  *   ex = f_BLF(D_x img) - D_x img,   ey = f_BLF(D_y img) - D_y img,
  * i.e. how far the bilateral filter moves each gradient field.  ex, ey: device [C][H][W]. */

@@ -17,12 +17,15 @@ from .blfls import (  # noqa: F401
     blfls_blf_residual,
     blfls_create,
     blfls_destroy,
+    blfls_gaussian,
     blfls_last_error,
     blfls_layers,
     blfls_smooth,
     blfls_smooth_batch,
+    blfls_smooth_guided,
     blfls_smooth_host,
     blfls_smooth_ls,
+    blfls_smooth_rolling,
     blfls_solve_residual,
     make_job,
 )

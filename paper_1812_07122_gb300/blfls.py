@@ -28,6 +28,7 @@ BLFLS_BF16W = 2
 BLFLS_DETAIL_ENHANCE = 0
 BLFLS_LOG_TONE = 1
 BLFLS_LOG_FLOOR = 1e-6
+BLFLS_MAX_GAUSS_SIGMA = 32.0
 
 BLFLS_MAX_DIM = 8192
 BLFLS_MAX_CHANNELS = 4
@@ -107,6 +108,11 @@ _SIGNATURES = {
     "blfls_smooth_ls": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp]),
     "blfls_layers": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_float, _c_float,
                               _c_float, _c_float, _c_int, _c_int, _c_int, _vp]),
+    "blfls_smooth_guided": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_float,
+                                     _c_float, _c_float, _c_int, _c_int, _c_int, _vp]),
+    "blfls_smooth_rolling": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
+                                      _c_float, _c_int, _c_int, _c_float, _c_int, _vp]),
+    "blfls_gaussian": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
 }
 
 
@@ -206,6 +212,29 @@ def blfls_layers(h, img, out, H, W, C, mode, strength, lam, sigma_s, sigma_r, ra
     _check(load().blfls_layers(h, _ptr(img), _ptr(out), int(H), int(W), int(C), int(mode),
                                float(strength), float(lam), float(sigma_s), float(sigma_r),
                                int(radius), int(iters), _prec(prec), _stream(stream)), h)
+
+
+def blfls_smooth_guided(h, img, guide, out, H, W, C, Cg, lam, sigma_s, sigma_r, radius, iters=1,
+                        prec=BLFLS_FP32, stream=None) -> None:
+    """Joint BLF-LS: range weights from the guidance image's gradients (Section III-D)."""
+    _check(load().blfls_smooth_guided(h, _ptr(img), _ptr(guide), _ptr(out), int(H), int(W),
+                                      int(C), int(Cg), float(lam), float(sigma_s),
+                                      float(sigma_r), int(radius), int(iters), _prec(prec),
+                                      _stream(stream)), h)
+
+
+def blfls_smooth_rolling(h, img, out, H, W, C, lam, sigma_s, sigma_r, radius, iters, sigma_g,
+                         prec=BLFLS_FP32, stream=None) -> None:
+    """Rolling guidance (Section III-D): first guidance = Gaussian(img, sigma_g)."""
+    _check(load().blfls_smooth_rolling(h, _ptr(img), _ptr(out), int(H), int(W), int(C),
+                                       float(lam), float(sigma_s), float(sigma_r), int(radius),
+                                       int(iters), float(sigma_g), _prec(prec), _stream(stream)), h)
+
+
+def blfls_gaussian(h, img, out, H, W, C, sigma, stream=None) -> None:
+    """Periodic separable Gaussian blur (the rolling guidance's first guidance)."""
+    _check(load().blfls_gaussian(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(sigma),
+                                 _stream(stream)), h)
 
 
 def blfls_blf_residual(h, img, ex, ey, H, W, C, sigma_s, sigma_r, radius, prec=BLFLS_FP32,

@@ -366,6 +366,7 @@ void blfls_destroy(blfls_handle* h)
     if (h->gscratch) cudaFree(h->gscratch);
     if (h->io) cudaFree(h->io);
     if (h->layer) cudaFree(h->layer);
+    if (h->gtmp) cudaFree(h->gtmp);
     delete h;
 }
 
@@ -486,6 +487,145 @@ int blfls_layers(blfls_handle* h, const float* img, float* out, int H, int W, in
         e = launch_layer_epilogue(1, h->layer, out, out, n, strength, s, h->num_sms);
     }
     return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "layer epilogue launch");
+}
+
+// Joint filter: channel c of a pass, with an optional guidance plane (nullptr = plain filter).
+static int joint_pass(blfls_handle* h, const float* src, const float* guide, float* dst,
+                      BlfParams bp, const SolveParams& sp, const FftPlanDev& rp,
+                      const FftPlanDev& cp, cudaStream_t s)
+{
+    bp.guide = guide;
+    bp.guide_stride = 0;
+    cudaError_t e = blf_launch(h, src, h->ex, h->ey, 1, bp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
+    e = solve_launch(h, src, h->ex, h->ey, dst, rp, cp, sp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+    return BLFLS_OK;
+}
+
+// Scratch of the joint filter: per-pixel kernel radii need the guidance's gradients too.
+static int prepare_joint(blfls_handle* h, int H, int W, int radius, const FftPlanDev** rp,
+                         const FftPlanDev** cp)
+{
+    int rc = prepare(h, H, W, radius, true, true, rp, cp);
+    if (rc != BLFLS_OK) return rc;
+    if (radius > blf_joint_tiled_max_radius())
+        rc = grow(h, h->gscratch, h->g_cap, 4 * (size_t)H * W, "gradients");
+    return rc;
+}
+
+static int check_sigma_g(float sigma)
+{
+    if (!(sigma > 0.f) || !(sigma <= BLFLS_MAX_GAUSS_SIGMA))
+        return fail(BLFLS_EINVAL, "sigma must lie in (0, BLFLS_MAX_GAUSS_SIGMA]");
+    return BLFLS_OK;
+}
+
+// Periodic Gaussian of C planes (in may equal out); the taps in FP64, stored FP32.
+static int gaussian_planes(blfls_handle* h, const float* in, float* out, int H, int W, int C,
+                           float sigma, cudaStream_t s)
+{
+    int rc;
+    const size_t plane = (size_t)H * W;
+    if ((rc = grow(h, h->gtmp, h->gtmp_cap, plane, "Gaussian scratch")) != BLFLS_OK) return rc;
+    const int R = (int)std::ceil(3.0 * (double)sigma);
+    std::vector<double> wd(2 * R + 1);
+    double sum = 0.0;
+    for (int k = -R; k <= R; ++k) sum += (wd[k + R] = std::exp(-(double)k * k / (2.0 * (double)sigma * sigma)));
+    std::vector<float> w(2 * R + 1);
+    for (int k = 0; k <= 2 * R; ++k) w[k] = (float)(wd[k] / sum);
+    for (int c = 0; c < C; ++c) {
+        const cudaError_t e = launch_gaussian(in + c * plane, h->gtmp, out + c * plane, H, W,
+                                              w.data(), R, s, h->num_sms);
+        if (e != cudaSuccess) return cuda_fail(e, "Gaussian kernel launch");
+    }
+    return BLFLS_OK;
+}
+
+int blfls_gaussian(blfls_handle* h, const float* img, float* out, int H, int W, int C, float sigma,
+                   void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_sigma_g(sigma)) != BLFLS_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    return gaussian_planes(h, img, out, H, W, C, sigma, static_cast<cudaStream_t>(stream));
+}
+
+int blfls_smooth_guided(blfls_handle* h, const float* img, const float* guide, float* out, int H,
+                        int W, int C, int Cg, float lambda, float sigma_s, float sigma_r,
+                        int radius, int iters, int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if (!guide) return fail(BLFLS_EINVAL, "guide is NULL");
+    if (Cg != 1 && Cg != C) return fail(BLFLS_EINVAL, "Cg must be 1 or C");
+    if (out == guide) return fail(BLFLS_EINVAL, "out must not alias guide");
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out == img) return BLFLS_OK;
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare_joint(h, H, W, radius, &rp, &cp)) != BLFLS_OK) return rc;
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int c = 0; c < C; ++c) {
+        const float* gc = guide + (Cg == 1 ? 0 : c * plane);
+        for (int it = 0; it < iters; ++it) {
+            const float* src = (it == 0 ? img : out) + c * plane;
+            if ((rc = joint_pass(h, src, gc, out + c * plane, bp, sp, *rp, *cp, s)) != BLFLS_OK) return rc;
+        }
+    }
+    return BLFLS_OK;
+}
+
+int blfls_smooth_rolling(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                         float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                         float sigma_g, int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if (out == img) return fail(BLFLS_EINVAL, "out must not alias img (every pass reads the input)");
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if ((rc = check_sigma_g(sigma_g)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    if ((rc = grow(h, h->layer, h->layer_cap, plane * C, "rolling guidance")) != BLFLS_OK) return rc;
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare_joint(h, H, W, radius, &rp, &cp)) != BLFLS_OK) return rc;
+    if ((rc = gaussian_planes(h, img, h->layer, H, W, C, sigma_g, s)) != BLFLS_OK) return rc;
+    const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int c = 0; c < C; ++c)
+        for (int it = 0; it < iters; ++it) {
+            // the bilateral kernel reads the whole guidance plane before K4 overwrites it
+            const float* gc = (it == 0 ? h->layer : out) + c * plane;
+            if ((rc = joint_pass(h, img + c * plane, gc, out + c * plane, bp, sp, *rp, *cp, s)) != BLFLS_OK)
+                return rc;
+        }
+    return BLFLS_OK;
 }
 
 int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, int H, int W,

@@ -1,5 +1,5 @@
-// K1 kernel instantiations of the F32 form, radii 0..16 (single-image and batched
-// drivers).  Split by precision so the three translation units compile in parallel.
+// K1 kernel instantiations of the F32 form, radii 0..16 (single-image, joint and
+// batched drivers).  Split by precision so the three translation units compile in parallel.
 #include "blf_tile.cuh"
 
 namespace blfls {
@@ -27,8 +27,20 @@ BatchFn pick_batch_f32(int r, bool range)
     }
 }
 
+template <int R>
+JointFn pick_joint_f32(int r)
+{
+    if constexpr (R > kMaxTemplR) {
+        return nullptr;
+    } else {
+        if (r != R) return pick_joint_f32<R + 1>(r);
+        return k1_blf_joint<R, 0>;
+    }
+}
+
 }  // namespace
 
+JointFn pick_joint_f32_entry(int r) { return pick_joint_f32<0>(r); }
 TiledFn pick_tiled_f32_entry(int r, bool range) { return pick_tiled_f32<0>(r, range); }
 BatchFn pick_batch_f32_entry(int r, bool range) { return pick_batch_f32<0>(r, range); }
 

@@ -12,6 +12,16 @@ TiledFn pick_tiled_bf16_entry(int r, bool range);
 BatchFn pick_batch_f32_entry(int r, bool range);
 BatchFn pick_batch_f16_entry(int r, bool range);
 BatchFn pick_batch_bf16_entry(int r, bool range);
+JointFn pick_joint_f32_entry(int r);
+JointFn pick_joint_f16_entry(int r);
+JointFn pick_joint_bf16_entry(int r);
+
+JointFn pick_joint_prec(int prec, int r)
+{
+    if (prec == 1) return pick_joint_f16_entry(r);
+    if (prec == 2) return pick_joint_bf16_entry(r);
+    return pick_joint_f32_entry(r);
+}
 
 TiledFn pick_tiled_prec(int prec, int r, bool range)
 {
@@ -106,18 +116,23 @@ __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ 
     }
 }
 
+// `hg`, when not null, holds the guidance image's gradients (same layout): the range weights
+// compare them instead of the input's (joint filter).
 template <bool RANGE>
-__global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ ex,
-                              float* __restrict__ ey, int H, int W, int R, float inv_kappa,
-                              float cs)
+__global__ void k1_blf_global(const float* __restrict__ g, const float* __restrict__ hg,
+                              float* __restrict__ ex, float* __restrict__ ey, int H, int W, int R,
+                              float inv_kappa, float cs)
 {
     const size_t plane = (size_t)H * W;
     const float* gx = g;
     const float* gy = g + plane;
+    const float* hx = hg ? hg : gx;
+    const float* hy = hg ? hg + plane : gy;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = int(i / W), x = int(i - (size_t)y * W);
         const float sx = gx[i], sy = gy[i];
+        const float hsx = hx[i], hsy = hy[i];
         float ax = 0.f, ay = 0.f, zx = 0.f, zy = 0.f;
         for (int dy = -R; dy <= R; ++dy) {
             const size_t row = (size_t)wrap_idx(y + dy, H) * W;
@@ -127,7 +142,7 @@ __global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ e
                 const float tx = __ldg(gx + t), ty = __ldg(gy + t);
                 float wx, wy;
                 if (RANGE) {
-                    const float qx = tx - sx, qy = ty - sy;
+                    const float qx = __ldg(hx + t) - hsx, qy = __ldg(hy + t) - hsy;
                     wx = ex2_approx(fmaf(-qx, qx, a));
                     wy = ex2_approx(fmaf(-qy, qy, a));
                 } else {
@@ -147,11 +162,12 @@ __global__ void k1_blf_global(const float* __restrict__ g, float* __restrict__ e
 
 }  // namespace
 
-size_t blf_templ_smem_bytes(int R, int prec, int th)
+size_t blf_templ_smem_bytes(int R, int prec, int th, bool joint)
 {
-    // one tile of (g_x, g_y) pairs: half2 for FP16W, float2 for FP32 and BF16W
+    // one tile of (g_x, g_y) pairs (two for the joint filter: input and guidance): half2 for
+    // FP16W, float2 for FP32 and BF16W
     const size_t pair = (prec == 1) ? sizeof(__half2) : sizeof(float2);
-    return f_bytes(R, th) + pair * (size_t)g_rows(R, th) * g_pitch(R);
+    return f_bytes(R, th) + (joint ? 2 : 1) * pair * (size_t)g_rows(R, th) * g_pitch(R);
 }
 
 int blf_tile_height(int th)
@@ -160,6 +176,7 @@ int blf_tile_height(int th)
 }
 
 int blf_tiled_max_radius() { return kMaxTiledR; }
+int blf_joint_tiled_max_radius() { return kMaxTemplR; }
 
 void init_blf_kernel_attributes()
 {
@@ -172,6 +189,10 @@ void init_blf_kernel_attributes()
                 cudaFuncSetAttribute(pick_batch_prec(prec, r, range),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)blf_templ_smem_bytes(r, prec, kMaxTH));
+                if (range)
+                    cudaFuncSetAttribute(pick_joint_prec(prec, r),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)blf_templ_smem_bytes(r, prec, kMaxTH, true));
             }
     const int rt = (int)tile_smem_bytes(kMaxTiledR, sizeof(float), 32);
     cudaFuncSetAttribute(k1_blf_tiled_rt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rt);
@@ -192,14 +213,20 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
                                 float* gscratch, cudaStream_t s)
 {
     const bool range = std::isfinite(p.sigma_r);
+    const bool joint = p.guide != nullptr && range;   // without a range kernel the guide is moot
     float kappa, inv_kappa, cs;
     blf_constants(p.sigma_s, p.sigma_r, &kappa, &inv_kappa, &cs);
     const int R = p.radius;
-    if (R <= kMaxTiledR) {
+    const size_t plane = (size_t)p.H * p.W;
+    if (joint ? R <= kMaxTemplR : R <= kMaxTiledR) {
         const int th = (R <= kMaxTemplR) ? blf_tile_height(p.tile_h) : 32;
         const int threads = kTW * th / kStrip;
         dim3 grid((p.W + kTW - 1) / kTW, (p.H + th - 1) / th, C);
-        if (R <= kMaxTemplR) {
+        if (joint) {
+            JointFn fn = pick_joint_prec(p.prec, R);
+            fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th, true), s>>>(
+                img, p.guide, p.guide_stride, ex, ey, p.H, p.W, th, kappa, inv_kappa, cs);
+        } else if (R <= kMaxTemplR) {
             TiledFn fn = pick_tiled_prec(p.prec, R, range);
             fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th), s>>>(img, ex, ey, p.H, p.W, th,
                                                                          kappa, inv_kappa, cs);
@@ -213,16 +240,18 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
         }
         return cudaGetLastError();
     }
+    // per-pixel kernel over gradients in global memory (the guidance's after the input's)
     if (p.prec != 0) return cudaErrorNotSupported;
     if (!gscratch) return cudaErrorInvalidValue;
-    const size_t plane = (size_t)p.H * p.W;
     const int blocks = (int)std::min<size_t>((plane + 255) / 256, 4096);
+    float* hg = joint ? gscratch + 2 * plane : nullptr;
     for (int c = 0; c < C; ++c) {
         k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kappa);
+        if (joint) k1_gradients<<<blocks, 256, 0, s>>>(p.guide + c * p.guide_stride, hg, p.H, p.W, kappa);
         if (range)
-            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, hg, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
         else
-            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, nullptr, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
     }
     return cudaGetLastError();
 }

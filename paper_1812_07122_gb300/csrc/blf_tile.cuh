@@ -164,8 +164,9 @@ __device__ __forceinline__ u64 bf2_to_f2(__nv_bfloat162 w)
     return pk(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
 }
 
-template <int R, bool RANGE, bool BF16W>
+template <int R, bool RANGE, bool BF16W, bool JOINT>
 __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
+                                                 const float* __restrict__ guide,
                                                  float* __restrict__ ex, float* __restrict__ ey,
                                                  int H, int W, int x0, int y0, int th,
                                                  float kappa, float inv_kappa, float cs,
@@ -175,18 +176,28 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
     const int gr = th + 2 * R;
     float* sf = reinterpret_cast<float*>(smem);
     float2* g = reinterpret_cast<float2*>(smem + f_bytes(R, th));   // (g_x', g_y') per position
+    float2* hg = JOINT ? g + gr * gp : g;                            // range-term values
     load_f_tile(f, H, W, x0, y0, R, th, sf);
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
         g[i] = make_float2(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
     }
+    if constexpr (JOINT) {   // the guidance image's gradients, through the same f buffer
+        __syncthreads();
+        load_f_tile(guide, H, W, x0, y0, R, th, sf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
+            const int r = i / gp, c = i - r * gp;
+            hg[i] = make_float2(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+        }
+    }
     __syncthreads();
 
     const int cx = threadIdx.x & (kTW - 1);
     const int r0 = (threadIdx.x / kTW) * kStrip;
     u64 S[kStrip], A[kStrip], Z[kStrip];
-    const u64* own = reinterpret_cast<const u64*>(g + (R + r0) * gp + R + cx);
+    const u64* own = reinterpret_cast<const u64*>(hg + (R + r0) * gp + R + cx);
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
         S[j] = own[j * gp];
@@ -206,9 +217,11 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
         const float gdx = ex2_approx(-float(dx * dx) * cs);     // the dx part of the weight
         const u64 GD = pk(gdx, gdx);
         const u64* col = reinterpret_cast<const u64*>(g + r0 * gp + R + cx + dx);
+        const u64* rcol = reinterpret_cast<const u64*>(hg + r0 * gp + R + cx + dx);
 #pragma unroll
         for (int i = 0; i < kStrip + 2 * R; ++i) {
             const u64 T = col[i * gp];
+            const u64 TR = JOINT ? rcol[i * gp] : T;   // the value the range weight compares
             const u64 TG = mul2(T, GD);
 #pragma unroll
             for (int j = 0; j < kStrip; ++j) {
@@ -216,7 +229,7 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
                 if (d < 0 || d > 2 * R) continue;
                 float e0, e1;
                 if (RANGE) {
-                    const u64 Q = sub2(T, S[j]);
+                    const u64 Q = sub2(TR, S[j]);
                     upk(fma2(Q, Q, NA[d]), e0, e1);
                 } else {
                     upk(NA[d], e0, e1);
@@ -230,31 +243,34 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
         }
     }
     float ax[kStrip], zx[kStrip], sx[kStrip], ay[kStrip], zy[kStrip], sy[kStrip];
+    const u64* own_g = reinterpret_cast<const u64*>(g + (R + r0) * gp + R + cx);
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
         upk(A[j], ax[j], ay[j]);
         upk(Z[j], zx[j], zy[j]);
-        upk(S[j], sx[j], sy[j]);
+        upk(JOINT ? own_g[j * gp] : S[j], sx[j], sy[j]);   // the input's own gradient
     }
     store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sx, ay, zy, sy, inv_kappa);
 }
 
-template <int R, bool RANGE>
-__device__ __forceinline__ void tile_f32(const float* __restrict__ f, float* __restrict__ ex,
+template <int R, bool RANGE, bool JOINT>
+__device__ __forceinline__ void tile_f32(const float* __restrict__ f, const float* __restrict__ guide,
+                                         float* __restrict__ ex,
                                          float* __restrict__ ey, int H, int W, int x0, int y0,
                                          int th, float kappa, float inv_kappa, float cs,
                                          unsigned char* smem)
 {
-    tile_pair_fields<R, RANGE, false>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    tile_pair_fields<R, RANGE, false, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
 }
 
-template <int R, bool RANGE>
-__device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __restrict__ ex,
+template <int R, bool RANGE, bool JOINT>
+__device__ __forceinline__ void tile_bf16(const float* __restrict__ f, const float* __restrict__ guide,
+                                          float* __restrict__ ex,
                                           float* __restrict__ ey, int H, int W, int x0, int y0,
                                           int th, float kappa, float inv_kappa, float cs,
                                           unsigned char* smem)
 {
-    tile_pair_fields<R, RANGE, true>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    tile_pair_fields<R, RANGE, true, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -263,8 +279,9 @@ __device__ __forceinline__ void tile_bf16(const float* __restrict__ f, float* __
 // column's sums of w t and w are kept in half2 and flushed into FP32 accumulators (scaled by
 // the column's spatial factor exp2(a_dx)) after every column.
 // ---------------------------------------------------------------------------------------------
-template <int R, bool RANGE>
-__device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __restrict__ ex,
+template <int R, bool RANGE, bool JOINT>
+__device__ __forceinline__ void tile_f16(const float* __restrict__ f, const float* __restrict__ guide,
+                                         float* __restrict__ ex,
                                          float* __restrict__ ey, int H, int W, int x0,
                                          int y0, int th, float kappa, float inv_kappa,
                                          float cs, unsigned char* smem)
@@ -273,13 +290,13 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __r
     const int gr = th + 2 * R;
     float* sf = reinterpret_cast<float*>(smem);
     __half2* g = reinterpret_cast<__half2*>(smem + f_bytes(R, th));   // (g_x', g_y') per position
+    __half2* hg = JOINT ? g + gr * gp : g;                            // range-term values
     load_f_tile(f, H, W, x0, y0, R, th, sf);
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
         g[i] = __floats2half2_rn(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
     }
-    __syncthreads();
 
     const int cx = threadIdx.x & (kTW - 1);
     const int r0 = (threadIdx.x / kTW) * kStrip;
@@ -288,11 +305,22 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __r
     float sxs[kStrip], sys[kStrip];
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
-        S[j] = g[(R + r0 + j) * gp + R + cx];
-        sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, kappa);   // FP32 centre values
+        sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, kappa);   // FP32 centre values of the input
         sys[j] = grad_y(sf, fp, R + r0 + j, R + cx, kappa);
         A[j] = Z[j] = 0ull;
     }
+    if constexpr (JOINT) {   // the guidance image's gradients, through the same f buffer
+        __syncthreads();
+        load_f_tile(guide, H, W, x0, y0, R, th, sf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
+            const int r = i / gp, c = i - r * gp;
+            hg[i] = __floats2half2_rn(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) S[j] = hg[(R + r0 + j) * gp + R + cx];
     // AD[d] = (a, a), a = -(d - R)^2 cs: the dy part of the spatial log2-weight of both lanes
     __half2 AD[2 * R + 1];
 #pragma unroll
@@ -310,16 +338,18 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __r
 #pragma unroll
         for (int j = 0; j < kStrip; ++j) P[j] = Q[j] = hz;
         const __half2* col = g + r0 * gp + R + cx + dx;
+        const __half2* rcol = hg + r0 * gp + R + cx + dx;
 #pragma unroll
         for (int i = 0; i < kStrip + 2 * R; ++i) {
             const __half2 T = col[i * gp];
+            const __half2 TR = JOINT ? rcol[i * gp] : T;   // the value the range weight compares
 #pragma unroll
             for (int j = 0; j < kStrip; ++j) {
                 const int d = i - j;  // dy + R
                 if (d < 0 || d > 2 * R) continue;
                 __half2 Wt;
                 if (RANGE) {
-                    const __half2 D = __hsub2(T, S[j]);
+                    const __half2 D = __hsub2(TR, S[j]);
                     Wt = ex2_h2(__hfma2(__hneg2(D), D, AD[d]));
                 } else {
                     Wt = ex2_h2(AD[d]);
@@ -344,14 +374,16 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, float* __r
     store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sxs, ay, zy, sys, inv_kappa);
 }
 
-template <int R, bool RANGE, int PREC>
-__device__ __forceinline__ void blf_tile(const float* f, float* ex, float* ey, int H, int W, int x0,
-                                         int y0, int th, float kappa, float inv_kappa, float cs,
-                                         unsigned char* smem)
+// JOINT: the range weights compare the gradients of `guide` (the joint filter of Section III-D);
+// the values averaged are still the gradients of f.
+template <int R, bool RANGE, int PREC, bool JOINT = false>
+__device__ __forceinline__ void blf_tile(const float* f, const float* guide, float* ex, float* ey,
+                                         int H, int W, int x0, int y0, int th, float kappa,
+                                         float inv_kappa, float cs, unsigned char* smem)
 {
-    if constexpr (PREC == 1) tile_f16<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
-    else if constexpr (PREC == 2) tile_bf16<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
-    else tile_f32<R, RANGE>(f, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    if constexpr (PREC == 1) tile_f16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    else if constexpr (PREC == 2) tile_bf16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    else tile_f32<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
 }
 
 // One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.
@@ -364,9 +396,28 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf(const float* __restrict__ 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t plane = (size_t)H * W;
-    blf_tile<R, RANGE, PREC>(img + blockIdx.z * plane, ex + blockIdx.z * plane,
+    blf_tile<R, RANGE, PREC>(img + blockIdx.z * plane, nullptr, ex + blockIdx.z * plane,
                              ey + blockIdx.z * plane, H, W, blockIdx.x * kTW, blockIdx.y * th,
                              th, kappa, inv_kappa, cs, smem);
+}
+
+// Joint form: as k1_blf with the range kernel on, guided by channel z of `guide` (channel
+// stride gstride floats; 0 shares one guidance channel among all channels).
+template <int R, int PREC>
+__global__ void __launch_bounds__(kMaxThreads) k1_blf_joint(const float* __restrict__ img,
+                                                            const float* __restrict__ guide,
+                                                            size_t gstride,
+                                                            float* __restrict__ ex,
+                                                            float* __restrict__ ey, int H, int W,
+                                                            int th, float kappa, float inv_kappa,
+                                                            float cs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t plane = (size_t)H * W;
+    blf_tile<R, true, PREC, true>(img + blockIdx.z * plane, guide + blockIdx.z * gstride,
+                                  ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W,
+                                  blockIdx.x * kTW, blockIdx.y * th, th, kappa, inv_kappa, cs,
+                                  smem);
 }
 
 // Batched form: a persistent grid walks every tile of every channel of the jobs of one
@@ -387,9 +438,9 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_batch(const BatchJob* __re
         const int ty = rem / J.tiles_x, tx = rem - ty * J.tiles_x;
         const size_t plane = (size_t)J.H * J.W;
         __syncthreads();   // the previous tile's readers are done with shared memory
-        blf_tile<R, RANGE, PREC>(J.src + c * plane, J.ex + c * plane, J.ey + c * plane, J.H, J.W,
-                                 tx * kTW, ty * J.tile_h, J.tile_h, J.kappa, J.inv_kappa, J.cs,
-                                 smem);
+        blf_tile<R, RANGE, PREC>(J.src + c * plane, nullptr, J.ex + c * plane, J.ey + c * plane,
+                                 J.H, J.W, tx * kTW, ty * J.tile_h, J.tile_h, J.kappa,
+                                 J.inv_kappa, J.cs, smem);
     }
 }
 
@@ -397,10 +448,13 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_batch(const BatchJob* __re
 
 using TiledFn = void (*)(const float*, float*, float*, int, int, int, float, float, float);
 using BatchFn = void (*)(const BatchJob*, const int2*, int, int);
+using JointFn = void (*)(const float*, const float*, size_t, float*, float*, int, int, int, float,
+                         float, float);
 
 // Kernel pointers of one precision (defined in blf_f32.cu, blf_f16.cu, blf_bf16.cu).
 TiledFn pick_tiled_prec(int prec, int r, bool range);
 BatchFn pick_batch_prec(int prec, int r, bool range);
-size_t blf_templ_smem_bytes(int R, int prec, int th);
+JointFn pick_joint_prec(int prec, int r);
+size_t blf_templ_smem_bytes(int R, int prec, int th, bool joint = false);
 
 }  // namespace blfls

@@ -31,8 +31,10 @@ struct blfls_handle {
     size_t g_cap = 0;
     float* io = nullptr;  // device copies for blfls_smooth_host: img then out
     size_t io_cap = 0;
-    float* layer = nullptr;  // blfls_layers: the smoothed (or logarithmic) image
+    float* layer = nullptr;  // blfls_layers: the smoothed (or logarithmic) image; rolling: guide
     size_t layer_cap = 0;
+    float* gtmp = nullptr;   // blfls_gaussian: one plane after the row pass
+    size_t gtmp_cap = 0;
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;

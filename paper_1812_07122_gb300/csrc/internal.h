@@ -96,16 +96,23 @@ struct BlfParams {
     float sigma_s, sigma_r;
     int prec;    // blfls_precision
     int tile_h;  // K1 tile height: 8, 16, 32 or 64 rows (others select 32)
+    // Joint filter (Section III-D): when set, the range weights compare the gradients of this
+    // image instead of the input's; channel c uses guide + c * guide_stride (0 = one shared
+    // guidance channel).
+    const float* guide = nullptr;
+    size_t guide_stride = 0;
 };
 
 // Launch K1 over channels [0, C) of img (planes of H*W floats).  `gscratch` must hold
-// 2*H*W floats when the radius is above the tiled kernels' limit (else may be null).
+// 2*H*W floats when the radius is above the tiled kernels' limit, 4*H*W for a joint filter of
+// radius above blf_joint_tiled_max_radius() (else it may be null).
 void init_blf_kernel_attributes();
 void init_solve_kernel_attributes();
 
 cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C,
                                 const BlfParams& p, float* gscratch, cudaStream_t s);
 int blf_tiled_max_radius();
+int blf_joint_tiled_max_radius();
 int blf_batch_max_radius();
 void blf_tiles(int H, int W, int tile_h, int* tiles_x, int* tiles_y);
 int blf_tile_height(int tile_h);   // the height actually used for a requested one
@@ -153,5 +160,10 @@ cudaError_t launch_log_image(const float* f, float* l, size_t n, float floor_v, 
                              int num_sms);
 cudaError_t launch_layer_epilogue(int mode, const float* f, const float* u, float* out, size_t n,
                                   float strength, cudaStream_t s, int num_sms);
+// Periodic separable Gaussian of one plane: rows of `in` into `tmp`, then columns into `out`;
+// taps w[0..2R] (sum 1), R <= kMaxGaussR.
+constexpr int kMaxGaussR = 96;
+cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int W, const float* w,
+                            int R, cudaStream_t s, int num_sms);
 
 }  // namespace blfls

@@ -8,8 +8,10 @@
 //   (Section IV).
 // * k5_layers: the epilogues of Section IV, detail enhancement out = f + m (f - u) and
 //   log-domain tone mapping out = exp(c b + (l - b)).
-// All three are HBM-bound streams (12 bytes per pixel); grid-stride loops over a persistent
-// grid of a few CTAs per SM.
+// * k5_gauss_rows / k5_gauss_cols: the periodic separable Gaussian that gives rolling guidance
+//   its first guidance image (Section III-D), rows then columns.
+// All are HBM-bound streams (12 bytes per pixel for the first three); grid-stride loops over a
+// persistent grid of a few CTAs per SM.
 #include <algorithm>
 
 #include "internal.h"
@@ -57,6 +59,47 @@ __global__ void __launch_bounds__(kStreamThreads) k5_layers(const float* f, cons
     }
 }
 
+struct GaussTaps {
+    int R;
+    float w[2 * kMaxGaussR + 1];
+};
+
+__device__ __forceinline__ int wrap_mod(int i, int n)
+{
+    const int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+__global__ void __launch_bounds__(kStreamThreads) k5_gauss_rows(const float* __restrict__ in,
+                                                               float* __restrict__ out, int H,
+                                                               int W, GaussTaps t)
+{
+    const size_t n = (size_t)H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
+        const float* row = in + (size_t)y * W;
+        float acc = 0.f;
+        for (int k = -t.R; k <= t.R; ++k) acc = fmaf(t.w[k + t.R], __ldg(row + wrap_mod(x + k, W)), acc);
+        out[i] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kStreamThreads) k5_gauss_cols(const float* __restrict__ in,
+                                                               float* __restrict__ out, int H,
+                                                               int W, GaussTaps t)
+{
+    const size_t n = (size_t)H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
+        float acc = 0.f;
+        for (int k = -t.R; k <= t.R; ++k)
+            acc = fmaf(t.w[k + t.R], __ldg(in + (size_t)wrap_mod(y + k, H) * W + x), acc);
+        out[i] = acc;
+    }
+}
+
 int stream_grid(size_t n, int num_sms)
 {
     const size_t want = (n + kStreamThreads - 1) / kStreamThreads;
@@ -84,6 +127,19 @@ cudaError_t launch_layer_epilogue(int mode, const float* f, const float* u, floa
                                   float strength, cudaStream_t s, int num_sms)
 {
     k5_layers<<<stream_grid(n, num_sms), kStreamThreads, 0, s>>>(f, u, out, n, mode, strength);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int W, const float* w,
+                            int R, cudaStream_t s, int num_sms)
+{
+    if (R < 0 || R > kMaxGaussR) return cudaErrorInvalidValue;
+    GaussTaps t;
+    t.R = R;
+    for (int k = 0; k <= 2 * R; ++k) t.w[k] = w[k];
+    const int grid = stream_grid((size_t)H * W, num_sms);
+    k5_gauss_rows<<<grid, kStreamThreads, 0, s>>>(in, tmp, H, W, t);
+    k5_gauss_cols<<<grid, kStreamThreads, 0, s>>>(tmp, out, H, W, t);
     return cudaGetLastError();
 }
 
