@@ -47,6 +47,46 @@ __device__ __forceinline__ void k2_build(const float* ex0, const float* ex1, con
                                          const float* ey0, const float* ey1, bool has1, int W,
                                          const FftPlanDev& rp, float2* data)
 {
+    if ((W & 3) == 0 && ((reinterpret_cast<uintptr_t>(ex0) | reinterpret_cast<uintptr_t>(ex1) |
+                          reinterpret_cast<uintptr_t>(eym) | reinterpret_cast<uintptr_t>(ey0) |
+                          reinterpret_cast<uintptr_t>(ey1)) & 15) == 0) {
+        // four pixels per thread from 16-byte loads; the padded positions of x..x+3 are
+        // contiguous when the padding block S is a multiple of 4 (or there is no padding)
+        const bool contig = (rp.pad_span & 3) == 0;
+        for (int q = threadIdx.x; q < (W >> 2); q += blockDim.x) {
+            const int x = q << 2;
+            const float4 a = *reinterpret_cast<const float4*>(ex0 + x);
+            const float4 m = *reinterpret_cast<const float4*>(eym + x);
+            const float4 e0 = *reinterpret_cast<const float4*>(ey0 + x);
+            const float l0 = ex0[x == 0 ? W - 1 : x - 1];
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f), e1 = b;
+            float l1 = 0.f;
+            if (has1) {
+                b = *reinterpret_cast<const float4*>(ex1 + x);
+                e1 = *reinterpret_cast<const float4*>(ey1 + x);
+                l1 = ex1[x == 0 ? W - 1 : x - 1];
+            }
+            // (D_x^T e_x)[x] = e_x[x-1] - e_x[x];  (D_y^T e_y)[y] = e_y[y-1] - e_y[y]
+            const float2 z0 = make_float2((l0 - a.x) + (m.x - e0.x), has1 ? (l1 - b.x) + (e0.x - e1.x) : 0.f);
+            const float2 z1 = make_float2((a.x - a.y) + (m.y - e0.y), has1 ? (b.x - b.y) + (e0.y - e1.y) : 0.f);
+            const float2 z2 = make_float2((a.y - a.z) + (m.z - e0.z), has1 ? (b.y - b.z) + (e0.z - e1.z) : 0.f);
+            const float2 z3 = make_float2((a.z - a.w) + (m.w - e0.w), has1 ? (b.z - b.w) + (e0.w - e1.w) : 0.f);
+            if (contig) {
+                float2* d = data + row_pos(rp, x);
+                d[0] = z0;
+                d[1] = z1;
+                d[2] = z2;
+                d[3] = z3;
+            } else {
+                data[row_pos(rp, x)] = z0;
+                data[row_pos(rp, x + 1)] = z1;
+                data[row_pos(rp, x + 2)] = z2;
+                data[row_pos(rp, x + 3)] = z3;
+            }
+        }
+        __syncthreads();
+        return;
+    }
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int xm = (x == 0) ? W - 1 : x - 1;
         // (D_x^T e_x)[y][x] = e_x[y][x-1] - e_x[y][x];  (D_y^T e_y)[y][x] = e_y[y-1][x] - e_y[y][x]
