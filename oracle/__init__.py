@@ -23,3 +23,4 @@ from .guided_ref import (  # noqa: F401
     gaussian,
     gaussian_weights,
 )
+from .grid_ref import blf_grid, blfls_grid, grid_shape  # noqa: F401
