@@ -21,6 +21,11 @@ notes), for one field g of size H x W with spatial and range parameters sigma_s,
    v = (interpolated sum of g) / (interpolated count).
 
 Image borders are open (the grid is not periodic), as in the grid method itself.
+
+The cell of a pixel is an integer decided by floating point, so it is decided in FP32 exactly as
+the CUDA kernel takes it: t = x / s_s (IEEE FP32 division) + 1/2, floor; z likewise from
+(g - min g) / s_r with g and min g in FP32.  Everything else (the sums, blur and interpolation)
+is FP64 on the values as given.
 """
 from __future__ import annotations
 
@@ -72,15 +77,19 @@ def blf_grid(g: np.ndarray, sigma_s: float, sigma_r: float) -> np.ndarray:
     """The bilateral-grid approximation of Eq. 1 on one field (FP64)."""
     g = np.asarray(g, dtype=np.float64)
     H, W = g.shape
-    lo, hi = float(g.min()), float(g.max())
-    gz, gy, gx = grid_shape(H, W, lo, hi, sigma_s, sigma_r)
-    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
-    zf = (g - lo) / sigma_r + PAD
-    yf = yy / sigma_s + PAD
-    xf = xx / sigma_s + PAD
-    cz = np.floor(zf + 0.5).astype(int)
-    cy = np.floor(yf + 0.5).astype(int)
-    cx = np.floor(xf + 0.5).astype(int)
+    g32 = g.astype(np.float32)
+    lo32, hi32 = g32.min(), g32.max()
+    ss32, sr32, half = np.float32(sigma_s), np.float32(sigma_r), np.float32(0.5)
+    gz, gy, gx = grid_shape(H, W, float(lo32), float(hi32), float(ss32), float(sr32))
+    yy, xx = np.mgrid[0:H, 0:W]
+    # cells: FP32 decisions (see the module notes)
+    cz = np.floor((g32 - lo32) / sr32 + half).astype(int) + PAD
+    cy = np.floor(yy.astype(np.float32) / ss32 + half).astype(int) + PAD
+    cx = np.floor(xx.astype(np.float32) / ss32 + half).astype(int) + PAD
+    # slicing coordinates: FP64 (continuous)
+    zf = (g32.astype(np.float64) - float(lo32)) / float(sr32) + PAD
+    yf = yy / float(ss32) + PAD
+    xf = xx / float(ss32) + PAD
     wi = np.zeros((gz, gy, gx))
     w = np.zeros((gz, gy, gx))
     np.add.at(wi, (cz, cy, cx), g)

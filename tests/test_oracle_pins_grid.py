@@ -36,10 +36,11 @@ def test_grid_unit_spatial_step_single_range_bin_is_normalised_convolution():
 
 
 def test_grid_is_affine_equivariant():
-    """(a g + b) with sigma_r scaled by a lands in the same cells: the output is a v + b."""
-    g = _rng(2).normal(scale=0.2, size=(20, 24))
-    v = oracle.blf_grid(g, 2.0, 0.1)
-    np.testing.assert_allclose(oracle.blf_grid(3.0 * g - 0.7, 2.0, 0.3), 3.0 * v - 0.7,
+    """(a g + b) with sigma_r scaled by a lands in the same cells: the output is a v + b.  The
+    values are dyadic and a is a power of two, so the FP32 cell decisions are exactly the same."""
+    g = _rng(2).integers(-16, 17, size=(20, 24)) / 64.0
+    v = oracle.blf_grid(g, 2.0, 0.125)
+    np.testing.assert_allclose(oracle.blf_grid(2.0 * g + 0.25, 2.0, 0.25), 2.0 * v + 0.25,
                                rtol=0, atol=1e-12)
 
 
