@@ -15,8 +15,8 @@ events the library records around each launch), ``e2e`` (host buffers through
 ``blfls_smooth_host``, copies included), ``clocks`` sampled by nvidia-smi during the timed loop,
 ``cpu_baseline`` (the FP64 oracle on the host cores, bounded sample, rank 0 at N=1 only) and
 ``forms`` (the FP16/BF16-weight precision forms on the same workload), ``modes`` (the LS model of
-Eq. 6, the detail-enhancement / log-tone applications of Section IV, and joint and rolling-
-guidance smoothing of Section III-D on the same image).
+Eq. 6, the detail-enhancement / log-tone applications of Section IV, joint and rolling-guidance
+smoothing of Section III-D, and BLF-LS on the bilateral-grid filter, on the same image).
 
 ``--impl reference`` times the FP64 oracle instead (the comparison arm; no GPU work).
 """
@@ -478,6 +478,12 @@ def main():
                  "log_tone_c0.5": timed_mp(tone, n),
                  "joint_guided_by_gaussian2": timed_mp(joint, n),
                  "rolling_guidance_sigma1": timed_mp(rolling, n)}
+        grid = lambda: blfls.blfls_smooth_grid(h, x, out, H, W, C, p["lam"], p["sigma_s"],
+                                               p["sigma_r"], p["iters"], stream)
+        try:
+            modes["bilateral_grid_blf"] = timed_mp(grid, n)
+        except blfls.BlflsError as e:
+            modes["bilateral_grid_blf"] = f"unavailable: {e}"
 
     batched = None
     if not args.no_batch:

@@ -162,6 +162,23 @@ int blfls_smooth_rolling(blfls_handle *h, const float *img, float *out, int H, i
 int blfls_gaussian(blfls_handle *h, const float *img, float *out, int H, int W, int C,
                    float sigma, void *stream);
 
+/* ---- BLF-LS with the bilateral-grid filter (the fast approximation the paper uses) -------- */
+
+#define BLFLS_GRID_MAX_BYTES (8ull << 30)
+
+/* BLF-LS (Eqs. 7-8) with each gradient field filtered by the bilateral-grid approximation of
+ * Eq. 1 (Paris and Durand's fast bilateral filter, which the paper's experiments use,
+ * Sections III-A and IV): sampling steps sigma_s in space and sigma_r in range, a 2-cell zero
+ * padding, splat to the nearest cell, 3-tap Gaussian blur of one cell along each grid axis,
+ * trilinear slice; open image borders in the grid (the solve stays periodic).  FP32.  Device
+ * pointers [C][H][W]; out may equal img.  Each pass reads the fields' ranges back to the host
+ * to size the grid, so the call synchronises `stream` once per pass.  sigma_s must be finite and
+ * >= 0.5; sigma_r may be +inf (one range cell).  Errors: BLFLS_EINVAL (arguments as
+ * blfls_smooth without radius and precision, sigma_s out of range, a grid above
+ * BLFLS_GRID_MAX_BYTES), BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_smooth_grid(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                      float lambda, float sigma_s, float sigma_r, int iters, void *stream);
+
 /* Step 1 alone (Eq. 1 on the gradients of Section II-B): for every channel,
  *   ex = f_BLF(D_x img) - D_x img,   ey = f_BLF(D_y img) - D_y img,
  * i.e. how far the bilateral filter moves each gradient field.  ex, ey: device [C][H][W]. */

@@ -22,6 +22,7 @@ from .blfls import (  # noqa: F401
     blfls_layers,
     blfls_smooth,
     blfls_smooth_batch,
+    blfls_smooth_grid,
     blfls_smooth_guided,
     blfls_smooth_host,
     blfls_smooth_ls,

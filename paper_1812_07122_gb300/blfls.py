@@ -113,6 +113,8 @@ _SIGNATURES = {
     "blfls_smooth_rolling": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
                                       _c_float, _c_int, _c_int, _c_float, _c_int, _vp]),
     "blfls_gaussian": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
+    "blfls_smooth_grid": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
+                                   _c_float, _c_int, _vp]),
 }
 
 
@@ -235,6 +237,12 @@ def blfls_gaussian(h, img, out, H, W, C, sigma, stream=None) -> None:
     """Periodic separable Gaussian blur (the rolling guidance's first guidance)."""
     _check(load().blfls_gaussian(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(sigma),
                                  _stream(stream)), h)
+
+
+def blfls_smooth_grid(h, img, out, H, W, C, lam, sigma_s, sigma_r, iters=1, stream=None) -> None:
+    """BLF-LS with the bilateral-grid approximation of the BLF (synchronises once per pass)."""
+    _check(load().blfls_smooth_grid(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(lam),
+                                    float(sigma_s), float(sigma_r), int(iters), _stream(stream)), h)
 
 
 def blfls_blf_residual(h, img, ex, ey, H, W, C, sigma_s, sigma_r, radius, prec=BLFLS_FP32,

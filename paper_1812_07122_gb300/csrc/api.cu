@@ -367,6 +367,9 @@ void blfls_destroy(blfls_handle* h)
     if (h->io) cudaFree(h->io);
     if (h->layer) cudaFree(h->layer);
     if (h->gtmp) cudaFree(h->gtmp);
+    if (h->grid_a) cudaFree(h->grid_a);
+    if (h->grid_keys) cudaFree(h->grid_keys);
+    if (h->grid_keys_host) cudaFreeHost(h->grid_keys_host);
     delete h;
 }
 
@@ -625,6 +628,88 @@ int blfls_smooth_rolling(blfls_handle* h, const float* img, float* out, int H, i
             if ((rc = joint_pass(h, img + c * plane, gc, out + c * plane, bp, sp, *rp, *cp, s)) != BLFLS_OK)
                 return rc;
         }
+    return BLFLS_OK;
+}
+
+// Both grid buffers in one allocation of 2 * cells float2.
+static int ensure_grid(blfls_handle* h, size_t cells)
+{
+    if (cells <= h->grid_cap && h->grid_a) return BLFLS_OK;
+    float2* p = h->grid_a;
+    size_t cap2 = 2 * h->grid_cap;
+    const int rc = grow(h, p, cap2, 2 * cells, "bilateral grid");
+    if (rc != BLFLS_OK) return rc;
+    h->grid_a = p;
+    h->grid_b = p + cells;
+    h->grid_cap = cells;
+    return BLFLS_OK;
+}
+
+int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                      float lambda, float sigma_s, float sigma_r, int iters, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if (!(sigma_s >= 0.5f) || !std::isfinite(sigma_s)) return fail(BLFLS_EINVAL, "sigma_s must be finite and >= 0.5");
+    if (!(sigma_r > 0.f)) return fail(BLFLS_EINVAL, "sigma_r must be > 0");
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out == img) return BLFLS_OK;
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare(h, H, W, 0, false, true, &rp, &cp)) != BLFLS_OK) return rc;
+    if ((rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "grid keys")) != BLFLS_OK)
+        return rc;
+    if (!h->grid_keys_host) {
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocHost(&p, sizeof(int) * 4 * BLFLS_MAX_CHANNELS);
+        if (e != cudaSuccess) return cuda_fail(e, "pinned grid keys");
+        h->grid_keys_host = static_cast<int*>(p);
+    }
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int it = 0; it < iters; ++it) {
+        const float* src = (it == 0) ? img : out;
+        // the ranges of both fields of every channel size the grids of this pass
+        cudaError_t e = launch_grid_minmax(src, H, W, C, h->grid_keys, s, h->num_sms);
+        if (e != cudaSuccess) return cuda_fail(e, "grid range kernel launch");
+        e = cudaMemcpyAsync(h->grid_keys_host, h->grid_keys, sizeof(int) * 4 * C,
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "grid range read-back");
+        float lo[2 * BLFLS_MAX_CHANNELS];
+        int dims[2 * BLFLS_MAX_CHANNELS][3];
+        size_t cells = 0;
+        for (int q = 0; q < 2 * C; ++q) {
+            lo[q] = grid_key_to_float(h->grid_keys_host[2 * q]);
+            const float hi = grid_key_to_float(h->grid_keys_host[2 * q + 1]);
+            grid_dims(H, W, lo[q], hi, sigma_s, sigma_r, &dims[q][0], &dims[q][1], &dims[q][2]);
+            cells = std::max(cells, (size_t)dims[q][0] * dims[q][1] * dims[q][2]);
+        }
+        if (2 * cells * sizeof(float2) > BLFLS_GRID_MAX_BYTES)
+            return fail(BLFLS_EINVAL, "bilateral grid above BLFLS_GRID_MAX_BYTES: raise sigma_s or sigma_r");
+        if ((rc = ensure_grid(h, cells)) != BLFLS_OK) return rc;
+        for (int c = 0; c < C; ++c) {
+            const float* fc = src + c * plane;
+            for (int field = 0; field < 2; ++field) {
+                const int q = 2 * c + field;
+                e = launch_grid_residual(fc, field == 0 ? h->ex : h->ey, field, H, W, sigma_s,
+                                         sigma_r, lo[q], dims[q][0], dims[q][1], dims[q][2],
+                                         h->grid_a, h->grid_b, s, h->num_sms);
+                if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
+            }
+            e = solve_launch(h, fc, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+        }
+    }
     return BLFLS_OK;
 }
 

@@ -35,6 +35,13 @@ struct blfls_handle {
     size_t layer_cap = 0;
     float* gtmp = nullptr;   // blfls_gaussian: one plane after the row pass
     size_t gtmp_cap = 0;
+    // blfls_smooth_grid: the two grid buffers, range keys on the device and their host copy
+    float2* grid_a = nullptr;
+    float2* grid_b = nullptr;
+    size_t grid_cap = 0;     // cells per buffer
+    int* grid_keys = nullptr;
+    size_t grid_keys_cap = 0;
+    int* grid_keys_host = nullptr;   // pinned, 4 * BLFLS_MAX_CHANNELS
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;

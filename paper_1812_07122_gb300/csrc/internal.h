@@ -166,4 +166,17 @@ constexpr int kMaxGaussR = 96;
 cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int W, const float* w,
                             int R, cudaStream_t s, int num_sms);
 
+// Bilateral-grid BLF (grid.cu).  launch_grid_minmax: keys[4c + 2 field + {0, 1}] receive the
+// order-preserving keys of min / max of field (0: x, 1: y) of channel c (decode with
+// grid_key_to_float).  launch_grid_residual: e = BLF_grid(g_field) - g_field for one channel;
+// ga, gb hold gx * gy * gz float2 each.
+cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys, cudaStream_t s,
+                               int num_sms);
+float grid_key_to_float(int key);
+void grid_dims(int H, int W, float lo, float hi, float sigma_s, float sigma_r, int* gx, int* gy,
+               int* gz);
+cudaError_t launch_grid_residual(const float* f, float* e, int field, int H, int W, float sigma_s,
+                                 float sigma_r, float lo, int gx, int gy, int gz, float2* ga,
+                                 float2* gb, cudaStream_t s, int num_sms);
+
 }  // namespace blfls
