@@ -24,3 +24,4 @@ from .guided_ref import (  # noqa: F401
     gaussian_weights,
 )
 from .grid_ref import blf_grid, blfls_grid, grid_shape  # noqa: F401
+from .nc_ref import domain_transform, nc_filter, nc_pass, nc_schedule, ncls  # noqa: F401
