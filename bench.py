@@ -16,7 +16,7 @@ events the library records around each launch), ``e2e`` (host buffers through
 ``cpu_baseline`` (the FP64 oracle on the host cores, bounded sample, rank 0 at N=1 only) and
 ``forms`` (the FP16/BF16-weight precision forms on the same workload), ``modes`` (the LS model of
 Eq. 6, the detail-enhancement / log-tone applications of Section IV, joint and rolling-guidance
-smoothing of Section III-D, and BLF-LS on the bilateral-grid filter, on the same image).
+smoothing of Section III-D, BLF-LS on the bilateral-grid filter, and NC-LS, on the same image).
 
 ``--impl reference`` times the FP64 oracle instead (the comparison arm; no GPU work).
 """
@@ -484,6 +484,9 @@ def main():
             modes["bilateral_grid_blf"] = timed_mp(grid, n)
         except blfls.BlflsError as e:
             modes["bilateral_grid_blf"] = f"unavailable: {e}"
+        nc = lambda: blfls.blfls_smooth_nc(h, x, out, H, W, C, p["lam"], p["sigma_s"],
+                                           p["sigma_r"], p["iters"], 3, stream)
+        modes["nc_ls_3_box_iterations"] = timed_mp(nc, n)
 
     batched = None
     if not args.no_batch:

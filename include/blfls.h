@@ -179,6 +179,24 @@ int blfls_gaussian(blfls_handle *h, const float *img, float *out, int H, int W, 
 int blfls_smooth_grid(blfls_handle *h, const float *img, float *out, int H, int W, int C,
                       float lambda, float sigma_s, float sigma_r, int iters, void *stream);
 
+/* ---- NC-LS (Section III-D) -------------------------------------------------------------- */
+
+#define BLFLS_MAX_NC_ITERS 8
+#define BLFLS_MAX_NC_SIGMA_S 256.0f
+
+/* NC-LS: BLF-LS with the bilateral filter on each gradient field replaced by the normalised
+ * convolution of the domain transform (Section III-D): per field g, the transform
+ * ct = running sum of 1 + (sigma_s / sigma_r) |g[j] - g[j-1]| along each row and each column
+ * (periodic lines; computed once per pass from the unfiltered field), then nc_iters box
+ * iterations of radius r_k = sigma_s sqrt(3) 2^(nc_iters-k) / sqrt(4^nc_iters - 1) sqrt(3) in the
+ * transformed domain, rows then columns; then the Fourier solve of Eq. 8.  FP32.  Device
+ * pointers [C][H][W], async; out may equal img.  sigma_s in (0, BLFLS_MAX_NC_SIGMA_S]; sigma_r
+ * > 0 (+inf: plain box iterations); nc_iters in [1, BLFLS_MAX_NC_ITERS] (3 is the usual choice).
+ * Errors: BLFLS_EINVAL, BLFLS_ENOMEM, BLFLS_ECUDA. */
+int blfls_smooth_nc(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                    float lambda, float sigma_s, float sigma_r, int iters, int nc_iters,
+                    void *stream);
+
 /* Step 1 alone (Eq. 1 on the gradients of Section II-B): for every channel,
  *   ex = f_BLF(D_x img) - D_x img,   ey = f_BLF(D_y img) - D_y img,
  * i.e. how far the bilateral filter moves each gradient field.  ex, ey: device [C][H][W]. */

@@ -115,6 +115,8 @@ _SIGNATURES = {
     "blfls_gaussian": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
     "blfls_smooth_grid": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
                                    _c_float, _c_int, _vp]),
+    "blfls_smooth_nc": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
+                                 _c_float, _c_int, _c_int, _vp]),
 }
 
 
@@ -243,6 +245,14 @@ def blfls_smooth_grid(h, img, out, H, W, C, lam, sigma_s, sigma_r, iters=1, stre
     """BLF-LS with the bilateral-grid approximation of the BLF (synchronises once per pass)."""
     _check(load().blfls_smooth_grid(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(lam),
                                     float(sigma_s), float(sigma_r), int(iters), _stream(stream)), h)
+
+
+def blfls_smooth_nc(h, img, out, H, W, C, lam, sigma_s, sigma_r, iters=1, nc_iters=3,
+                    stream=None) -> None:
+    """NC-LS: the domain-transform normalised convolution in place of the BLF."""
+    _check(load().blfls_smooth_nc(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(lam),
+                                  float(sigma_s), float(sigma_r), int(iters), int(nc_iters),
+                                  _stream(stream)), h)
 
 
 def blfls_blf_residual(h, img, ex, ey, H, W, C, sigma_s, sigma_r, radius, prec=BLFLS_FP32,

@@ -370,6 +370,7 @@ void blfls_destroy(blfls_handle* h)
     if (h->grid_a) cudaFree(h->grid_a);
     if (h->grid_keys) cudaFree(h->grid_keys);
     if (h->grid_keys_host) cudaFreeHost(h->grid_keys_host);
+    if (h->nc_scratch) cudaFree(h->nc_scratch);
     delete h;
 }
 
@@ -710,6 +711,46 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
             if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
         }
     }
+    return BLFLS_OK;
+}
+
+int blfls_smooth_nc(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                    float lambda, float sigma_s, float sigma_r, int iters, int nc_iters,
+                    void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if (!(sigma_s > 0.f) || !(sigma_s <= BLFLS_MAX_NC_SIGMA_S))
+        return fail(BLFLS_EINVAL, "sigma_s must lie in (0, BLFLS_MAX_NC_SIGMA_S]");
+    if (!(sigma_r > 0.f)) return fail(BLFLS_EINVAL, "sigma_r must be > 0");
+    if (nc_iters < 1 || nc_iters > BLFLS_MAX_NC_ITERS) return fail(BLFLS_EINVAL, "nc_iters must lie in [1, BLFLS_MAX_NC_ITERS]");
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out == img) return BLFLS_OK;
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare(h, H, W, 0, false, true, &rp, &cp)) != BLFLS_OK) return rc;
+    if ((rc = grow(h, h->nc_scratch, h->nc_cap, nc_scratch_floats(H, W), "NC scratch")) != BLFLS_OK)
+        return rc;
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int c = 0; c < C; ++c)
+        for (int it = 0; it < iters; ++it) {
+            const float* src = (it == 0 ? img : out) + c * plane;
+            cudaError_t e = launch_nc_residuals(src, h->ex, h->ey, H, W, sigma_s, sigma_r,
+                                                nc_iters, h->nc_scratch, s, h->num_sms);
+            if (e != cudaSuccess) return cuda_fail(e, "NC kernel launch");
+            e = solve_launch(h, src, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+        }
     return BLFLS_OK;
 }
 

@@ -42,6 +42,8 @@ struct blfls_handle {
     int* grid_keys = nullptr;
     size_t grid_keys_cap = 0;
     int* grid_keys_host = nullptr;   // pinned, 4 * BLFLS_MAX_CHANNELS
+    float* nc_scratch = nullptr;     // blfls_smooth_nc: gradients, transforms, two buffers
+    size_t nc_cap = 0;
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;

@@ -179,4 +179,11 @@ cudaError_t launch_grid_residual(const float* f, float* e, int field, int H, int
                                  float sigma_r, float lo, int gx, int gy, int gz, float2* ga,
                                  float2* gb, cudaStream_t s, int num_sms);
 
+// NC-LS (nc.cu): ex, ey = NC(g) - g for one channel f, n_iter box iterations; `scratch` holds
+// nc_scratch_floats(H, W) floats.
+cudaError_t launch_nc_residuals(const float* f, float* ex, float* ey, int H, int W,
+                                float sigma_s, float sigma_r, int n_iter, float* scratch,
+                                cudaStream_t s, int num_sms);
+size_t nc_scratch_floats(int H, int W);
+
 }  // namespace blfls
