@@ -201,8 +201,9 @@ def bench_batched(h, dev, stream, flush, steps):
     from paper_1812_07122_gb300 import blfls, synth
     jobs = synth.batch_jobs(64, seed=4)
     for r in sorted({j.radius for j in jobs}):
-        blfls.blfls_autotune(h, 768, 1024, 1, r, 0, None)
-    xs, ys, cj = [], [], []
+        for prec in (0, 1):
+            blfls.blfls_autotune(h, 768, 1024, 1, r, prec, None)
+    xs, ys, cj, cj16 = [], [], [], []
     for j in jobs:
         x = torch.from_numpy(synth.job_image(j)).to(dev)
         y = torch.empty_like(x)
@@ -210,6 +211,8 @@ def bench_batched(h, dev, stream, flush, steps):
         ys.append(y)
         cj.append(blfls.make_job(x, y, j.H, j.W, j.C, j.lam, j.sigma_s, j.sigma_r, j.radius,
                                  j.iters))
+        cj16.append(blfls.make_job(x, y, j.H, j.W, j.C, j.lam, j.sigma_s, j.sigma_r, j.radius,
+                                   j.iters, blfls.BLFLS_FP16W))
     mp = sum(j.H * j.W for j in jobs) / 1e6
 
     def loop():
@@ -219,6 +222,9 @@ def bench_batched(h, dev, stream, flush, steps):
 
     def batch():
         blfls.blfls_smooth_batch(h, cj, stream)
+
+    def batch16():
+        blfls.blfls_smooth_batch(h, cj16, stream)
 
     def timed(fn, n):
         for _ in range(3):
@@ -238,13 +244,17 @@ def bench_batched(h, dev, stream, flush, steps):
     n = max(3, steps // 6)
     t_batch = timed(batch, n)
     t_loop = timed(loop, n)
+    t_batch16 = timed(batch16, n)
     return {"workload": "64 jobs, H log-uniform 256-1536, W 256-2048, C in {1,3}, lambda~U[5,50], "
                         "sigma_r~U[0.05,0.2], radius in {3,5,8,10}, sigma_s=r/2, 1 pass, FP32",
             "megapixels_per_call": round(mp, 2), "ms_batched": round(t_batch, 3),
             "ms_single_loop": round(t_loop, 3), "batched_mp_per_s": round(mp / t_batch * 1e3, 1),
             "single_loop_mp_per_s": round(mp / t_loop * 1e3, 1),
-            "speedup": round(t_loop / t_batch, 3), "launch": "graph replay of one persistent "
-                        "launch per phase (K1 per radius group, K2, K3, K4)"}
+            "speedup": round(t_loop / t_batch, 3),
+            "batched_fp16w_mp_per_s": round(mp / t_batch16 * 1e3, 1),
+            "batched_fp16w_speedup_vs_fp32_loop": round(t_loop / t_batch16, 3),
+            "launch": "graph replay of one persistent launch per phase (K1 per radius group, "
+                      "K2, K3, K4)"}
 
 
 def bench_serving(dev, n_req, rate):
