@@ -25,6 +25,9 @@
 
 namespace blfls {
 
+// Shared-memory cap of one column block in the batched column kernel (see run_batch).
+constexpr size_t kBatchColBytes = 32 * 1024;
+
 struct BatchState {
     void* arena = nullptr;   // residuals and spectra of all batched jobs (device)
     size_t arena_cap = 0;
@@ -182,6 +185,10 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
             if ((rc = get_plan(h, j.H, &I.cp)) != BLFLS_OK) return rc;
             blf_constants(j.sigma_s, j.sigma_r, &I.kappa, &I.inv_kappa, &I.cs);
             I.lgc = solve_fit_lgc(I.cp->L, tuned_col_block(h, I.cp->L));
+            // The batched column kernel takes the largest block of the batch as its shared
+            // memory, so cap every job's block at kBatchColBytes: one long (e.g. Bluestein)
+            // column set must not cut the occupancy of every other job's items.
+            while (I.lgc > 0 && (sizeof(float2) * (size_t)I.cp->L << I.lgc) > kBatchColBytes) --I.lgc;
             I.tile_h = blf_tile_height(tuned_tile_h(h, j.radius, j.prec));
             blf_tiles(j.H, j.W, I.tile_h, &I.tiles_x, &I.tiles_y);
             const size_t planes = (size_t)j.C * j.H * j.W;

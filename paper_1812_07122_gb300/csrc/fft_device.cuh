@@ -12,8 +12,8 @@
 //   inverse: the conjugate stages in reverse order, digit-reversed input -> natural output,
 //            unnormalised (a forward-then-inverse pair multiplies by L).
 // Bluestein transforms (length N not 7-smooth) convert the length-N DFT into a cyclic
-// convolution of length L = 2^k >= 2N-1 carried out by the direct transforms; input and output
-// are in natural order, positions [N, L) are scratch.
+// convolution of length L >= 2N-1 (the smallest 7-smooth such L) carried out by the direct
+// transforms; input and output are in natural order, positions [N, L) are scratch.
 #pragma once
 
 #include "internal.h"

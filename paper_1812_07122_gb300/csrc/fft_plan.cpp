@@ -2,6 +2,7 @@
 // Bluestein chirps.  Every table is computed in FP64 on the host and stored as FP32.
 #include "internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -32,26 +33,52 @@ std::vector<int> dif_positions(int N, const std::vector<int>& radices)
     return pos;
 }
 
-// Plain FP64 radix-2 FFT (length a power of two), forward sign exp(-2 pi i nk/N).
-void host_fft_pow2(std::vector<std::complex<double>>& a)
+// Plain FP64 mixed-radix FFT for lengths whose prime factors are 2, 3, 5 and 7 (recursive
+// decimation in time: n = p m with p the smallest prime factor), forward sign exp(-2 pi i nk/N).
+void host_fft_smooth(std::vector<std::complex<double>>& a)
 {
     const size_t n = a.size();
-    for (size_t i = 1, j = 0; i < n; ++i) {
-        size_t bit = n >> 1;
-        for (; j & bit; bit >>= 1) j ^= bit;
-        j ^= bit;
-        if (i < j) std::swap(a[i], a[j]);
-    }
-    for (size_t len = 2; len <= n; len <<= 1) {
-        for (size_t i = 0; i < n; i += len) {
-            for (size_t k = 0; k < len / 2; ++k) {
-                const double ang = -2.0 * kPi * double(k) / double(len);
-                const std::complex<double> w(std::cos(ang), std::sin(ang));
-                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
-                a[i + k] = u + v;
-                a[i + k + len / 2] = u - v;
+    if (n <= 1) return;
+    size_t p = 0;
+    for (size_t q : {2, 3, 5, 7})
+        if (n % q == 0) { p = q; break; }
+    if (p == 0) {   // not 7-smooth: plain DFT (not reached by the plans built here)
+        std::vector<std::complex<double>> out(n);
+        for (size_t k = 0; k < n; ++k)
+            for (size_t t = 0; t < n; ++t) {
+                const double ang = -2.0 * kPi * double((k * t) % n) / double(n);
+                out[k] += a[t] * std::complex<double>(std::cos(ang), std::sin(ang));
             }
+        a = out;
+        return;
+    }
+    const size_t m = n / p;
+    std::vector<std::vector<std::complex<double>>> sub(p, std::vector<std::complex<double>>(m));
+    for (size_t r = 0; r < p; ++r)
+        for (size_t t = 0; t < m; ++t) sub[r][t] = a[t * p + r];
+    for (size_t r = 0; r < p; ++r) host_fft_smooth(sub[r]);
+    // X[k + m q] = sum_r w_n^(r (k + m q)) S_r[k]
+    for (size_t k = 0; k < m; ++k)
+        for (size_t q = 0; q < p; ++q) {
+            const size_t kk = k + m * q;
+            std::complex<double> acc = 0.0;
+            for (size_t r = 0; r < p; ++r) {
+                const double ang = -2.0 * kPi * double((r * kk) % n) / double(n);
+                acc += sub[r][k] * std::complex<double>(std::cos(ang), std::sin(ang));
+            }
+            a[kk] = acc;
         }
+}
+
+// Work length of a Bluestein transform of length N: the smallest 7-smooth L >= 2N - 1 (the
+// cyclic convolution needs L >= 2N - 1; the direct FFT handles every 7-smooth length).
+int bluestein_length(int N)
+{
+    for (int L = std::max(1, 2 * N - 1);; ++L) {
+        int r = L;
+        for (int q : {2, 3, 5, 7})
+            while (r % q == 0) r /= q;
+        if (r == 1) return L;
     }
 }
 
@@ -116,9 +143,8 @@ cudaError_t build_fft_plan(int N, FftPlanHost& out)
     const bool direct = factor_direct(N, radices);
     int L = N;
     if (!direct) {
-        L = 1;
-        while (L < 2 * N - 1) L <<= 1;
-        factor_direct(L, radices);
+        L = bluestein_length(N);
+        if (!factor_direct(L, radices)) return cudaErrorInvalidValue;
     }
     if (L > kMaxFftLen) return cudaErrorInvalidValue;
     d.L = L;
@@ -157,7 +183,7 @@ cudaError_t build_fft_plan(int N, FftPlanHost& out)
             b[n] = std::conj(c[n]);
             if (n > 0) b[L - n] = std::conj(c[n]);
         }
-        host_fft_pow2(b);
+        host_fft_smooth(b);
         bhat.resize(L);
         for (int k = 0; k < L; ++k) {
             const std::complex<double> v = b[k] / double(L);
@@ -224,9 +250,8 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     const bool direct = factor_direct(N, radices);
     int L = N;
     if (!direct) {
-        L = 1;
-        while (L < 2 * N - 1) L <<= 1;
-        factor_direct(L, radices);
+        L = bluestein_length(N);
+        if (!factor_direct(L, radices)) return false;
     }
     if (L > kMaxFftLen) return false;
     rel.L = L;
@@ -263,7 +288,7 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
             b[n] = std::conj(c[n]);
             if (n > 0) b[L - n] = std::conj(c[n]);
         }
-        host_fft_pow2(b);
+        host_fft_smooth(b);
         bhat.resize(L);
         for (int k = 0; k < L; ++k) {
             const std::complex<double> v = b[k] / double(L);

@@ -11,12 +11,13 @@ namespace blfls {
 
 // ---------------------------------------------------------------------------------------------
 // FFT plans.  A transform of length N is either a direct in-place mixed-radix FFT (N factors
-// into 16, 8, 4, 2, 3, 5, 7) or Bluestein's chirp-z algorithm over a direct power-of-two FFT of length
-// L >= 2N - 1.  The direct forward transform is decimation in frequency: natural-order input,
-// output in mixed-radix digit-reversed order, so frequency k sits at position perm[k].  The
-// inverse runs the conjugate stages in reverse order and takes that order back to natural.
-// Bluestein transforms use natural order on both sides (perm is the identity for its users).
-// All tables are computed in FP64 on the host and stored as FP32 (complex as float2).
+// into 16, 15, 9, 8, 4, 2, 3, 5, 7) or Bluestein's chirp-z algorithm over a direct FFT of the
+// smallest 7-smooth length L >= 2N - 1.  The direct forward transform is decimation in
+// frequency: natural-order input, output in mixed-radix digit-reversed order, so frequency k
+// sits at position perm[k].  The inverse runs the conjugate stages in reverse order and takes
+// that order back to natural.  Bluestein transforms use natural order on both sides (perm is
+// the identity for its users).  All tables are computed in FP64 on the host and stored as FP32
+// (complex as float2).
 // ---------------------------------------------------------------------------------------------
 constexpr int kMaxStages = 16;
 constexpr int kMaxFftLen = 16384;  // longest direct transform (Bluestein work length)
