@@ -77,6 +77,7 @@ struct Pass {
     std::vector<int2> rows, cols;
     int total_rows = 0, total_cols = 0;
     size_t smem_rows = 0, smem_cols = 0;
+    int max_w = 0;   // widest row of the pass (sizes the staged row drivers)
     // byte offsets inside the uploaded blob
     size_t o_table = 0, o_rows = 0, o_cols = 0;
     std::vector<size_t> o_groups;
@@ -130,7 +131,7 @@ cudaError_t enqueue(blfls_handle* h, const std::vector<Pass>& passes)
         for (int g = 1; g < ng; ++g) cudaStreamWaitEvent(b->main, b->ev_join[g - 1], 0);
         e = launch_solve_batch(tab, (int)p.table.size(), reinterpret_cast<const int2*>(dev + p.o_rows),
                                p.total_rows, reinterpret_cast<const int2*>(dev + p.o_cols),
-                               p.total_cols, p.smem_rows, p.smem_cols, h->num_sms, b->main);
+                               p.total_cols, p.smem_rows, p.smem_cols, p.max_w, h->num_sms, b->main);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -254,6 +255,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
                 P.cols.push_back(make_int2(entry, P.total_cols));
                 P.total_cols += j.C * ((j.W / 2 + 1 + (1 << I.lgc) - 1) >> I.lgc);
                 P.smem_rows = std::max(P.smem_rows, sizeof(float2) * (size_t)row_buf_elems(*I.rp));
+                P.max_w = std::max(P.max_w, j.W);
                 P.smem_cols = std::max(P.smem_cols, (sizeof(float2) * (size_t)I.cp->L) << I.lgc);
             }
             max_groups = std::max(max_groups, (int)P.groups.size());
@@ -307,6 +309,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
             sig.push_back(P.total_rows);
             sig.push_back(P.total_cols);
             sig.push_back((long long)P.smem_rows);
+            sig.push_back((long long)P.max_w);
             sig.push_back((long long)P.smem_cols);
             sig.push_back((long long)P.o_table);
             sig.push_back((long long)P.o_rows);

@@ -151,8 +151,8 @@ int solve_fit_lgc(int L, int col_block);
 // shared memory any job needs in that phase.
 cudaError_t launch_solve_batch(const BatchJob* jobs, int njobs, const int2* grp_rows,
                                int total_rows, const int2* grp_cols, int total_cols,
-                               size_t smem_rows, size_t smem_cols, int num_sms, cudaStream_t s,
-                               const cudaEvent_t* marks = nullptr);
+                               size_t smem_rows, size_t smem_cols, int max_w, int num_sms,
+                               cudaStream_t s, const cudaEvent_t* marks = nullptr);
 
 // Elementwise kernels of the LS model and of the base/detail applications (layers.cu).
 cudaError_t launch_ls_residuals(const float* f, float* ex, float* ey, int H, int W,

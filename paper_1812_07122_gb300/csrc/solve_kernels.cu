@@ -578,6 +578,147 @@ __global__ void __launch_bounds__(512) k4_batch(const BatchJob* __restrict__ job
     }
 }
 
+// ---- batched, staged: the row drivers of the single image over the row pairs of many jobs,
+// taken with a grid stride; the staging buffer and the FFT buffer are sized for the widest row
+// of the batch. ---------------------------------------------------------------------------------
+
+// Row pair `item` of the jobs: job entry, channel plane offset and pair index.
+struct RowItem {
+    const BatchJob* J;
+    int c, pair;
+};
+
+__device__ __forceinline__ RowItem row_item(const BatchJob* __restrict__ jobs,
+                                            const int2* __restrict__ grp, int ngrp, int item,
+                                            int& g)
+{
+    while (g + 1 < ngrp && __ldg(&grp[g + 1].y) <= item) ++g;
+    const BatchJob* J = jobs + __ldg(&grp[g].x);
+    const int npairs = (J->H + 1) / 2;
+    const int local = item - __ldg(&grp[g].y);
+    const int c = local / npairs;
+    return RowItem{J, c, local - c * npairs};
+}
+
+__device__ __forceinline__ bool aligned16(const void* p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+__global__ void __launch_bounds__(kStagedThreads, 2) k2_batch_staged(const BatchJob* __restrict__ jobs,
+                                                                     const int2* __restrict__ grp,
+                                                                     int ngrp, int total, int Wp)
+{
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    float* st = reinterpret_cast<float*>(staged_smem);
+    float2* data = reinterpret_cast<float2*>(staged_smem + sizeof(float) * 5 * (size_t)Wp);
+    // items blockIdx.x, blockIdx.x + gridDim.x, ...: the costs of the jobs' row pairs differ
+    // widely (widths, Bluestein rows), and a stride spreads them evenly over the CTAs
+    const int i0 = blockIdx.x, step = gridDim.x;
+    if (i0 >= total) return;
+    int gc = 0, gn = 0;   // group cursors of the current and the next item
+    auto issue = [&](const RowItem& it) {
+        const BatchJob& J = *it.J;
+        const int H = J.H, W = J.W;
+        const size_t plane = (size_t)H * W;
+        const float* ex = J.ex + it.c * plane;
+        const float* ey = J.ey + it.c * plane;
+        const int y0 = 2 * it.pair, y1 = y0 + 1;
+        const int ym = (y0 == 0) ? H - 1 : y0 - 1;
+        const bool vec = (W & 3) == 0 && aligned16(ex) && aligned16(ey);
+        stage_floats(st, ex + (size_t)y0 * W, W, vec);
+        stage_floats(st + 2 * Wp, ey + (size_t)ym * W, W, vec);
+        stage_floats(st + 3 * Wp, ey + (size_t)y0 * W, W, vec);
+        if (y1 < H) {
+            stage_floats(st + Wp, ex + (size_t)y1 * W, W, vec);
+            stage_floats(st + 4 * Wp, ey + (size_t)y1 * W, W, vec);
+        }
+        cp_commit();
+    };
+    RowItem cur = row_item(jobs, grp, ngrp, i0, gc);
+    gn = gc;
+    issue(cur);
+    for (int item = i0; item < total; item += step) {
+        cp_wait<0>();
+        __syncthreads();
+        const BatchJob& J = *cur.J;
+        const int W = J.W, Wh = W / 2 + 1;
+        const int y0 = 2 * cur.pair, y1 = y0 + 1;
+        const bool has1 = y1 < J.H;
+        k2_build(st, st + Wp, st + 2 * Wp, st + 3 * Wp, st + 4 * Wp, has1, W, J.rp, data);
+        RowItem next{};
+        if (item + step < total) {
+            next = row_item(jobs, grp, ngrp, item + step, gn);
+            issue(next);   // the rows of this pair have been read out
+        }
+        float2* spec = J.spec + cur.c * (size_t)J.H * Wh;
+        k2_transform(has1, W, spec + (size_t)y0 * Wh, spec + (size_t)(has1 ? y1 : y0) * Wh, J.rp,
+                     J.rp.tw, data);
+        cur = next;
+    }
+}
+
+__global__ void __launch_bounds__(kStagedThreads, 2) k4_batch_staged(const BatchJob* __restrict__ jobs,
+                                                                     const int2* __restrict__ grp,
+                                                                     int ngrp, int total, int Wp)
+{
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    const size_t spec_bytes = align16(sizeof(float2) * 2 * (size_t)(Wp / 2 + 1));
+    float2* ss = reinterpret_cast<float2*>(staged_smem);
+    float* sf = reinterpret_cast<float*>(staged_smem + spec_bytes);
+    float2* data = reinterpret_cast<float2*>(staged_smem + spec_bytes + sizeof(float) * 2 * (size_t)Wp);
+    const int i0 = blockIdx.x, step = gridDim.x;   // strided items, as in k2_batch_staged
+    if (i0 >= total) return;
+    int gc = 0, gn = 0;
+    auto issue_spec = [&](const RowItem& it) {
+        const BatchJob& J = *it.J;
+        const int Wh = J.W / 2 + 1;
+        const float2* spec = J.spec + it.c * (size_t)J.H * Wh;
+        const int y0 = 2 * it.pair, y1 = y0 + 1;
+        stage_complex(ss, spec + (size_t)y0 * Wh, Wh);
+        if (y1 < J.H) stage_complex(ss + Wh, spec + (size_t)y1 * Wh, Wh);
+        cp_commit();
+    };
+    auto issue_f = [&](const RowItem& it) {
+        const BatchJob& J = *it.J;
+        const int W = J.W;
+        const float* f = J.src + it.c * (size_t)J.H * W;
+        const int y0 = 2 * it.pair, y1 = y0 + 1;
+        const bool vec = (W & 3) == 0 && aligned16(f);
+        stage_floats(sf, f + (size_t)y0 * W, W, vec);
+        if (y1 < J.H) stage_floats(sf + Wp, f + (size_t)y1 * W, W, vec);
+        cp_commit();
+    };
+    // copy groups complete in issue order: spectra(p), f(p), spectra(p+1), f(p+1), ...
+    RowItem cur = row_item(jobs, grp, ngrp, i0, gc);
+    gn = gc;
+    issue_spec(cur);
+    issue_f(cur);
+    for (int item = i0; item < total; item += step) {
+        cp_wait<1>();   // spectra of this pair landed; its f may still be in flight
+        __syncthreads();
+        const BatchJob& J = *cur.J;
+        const int W = J.W, Wh = W / 2 + 1;
+        const int y0 = 2 * cur.pair, y1 = y0 + 1;
+        const bool has1 = y1 < J.H;
+        k4_rebuild(ss, ss + Wh, has1, W, J.rp, data);
+        const bool more = item + step < total;
+        RowItem next{};
+        if (more) {
+            next = row_item(jobs, grp, ngrp, item + step, gn);
+            issue_spec(next);   // the spectra of this pair have been read out
+        }
+        fft_inverse<0, true>(data, 0, J.rp, J.rp.tw);
+        if (more) cp_wait<1>(); else cp_wait<0>();   // f of this pair landed
+        __syncthreads();
+        float* out = J.dst + cur.c * (size_t)J.H * W;
+        k4_output(has1, sf, sf + Wp, out + (size_t)y0 * W, out + (size_t)(has1 ? y1 : y0) * W, W,
+                  J.rp, data);
+        if (more) issue_f(next);
+        cur = next;
+    }
+}
+
 int threads_for(int work)
 {
     int t = 128;
@@ -602,6 +743,8 @@ void init_solve_kernel_attributes()
     cudaFuncSetAttribute(k3_cols_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k3_cols_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k2_batch_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k4_batch_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 size_t solve_smem_rows(const FftPlanDev& rp)
@@ -738,21 +881,40 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
 
 cudaError_t launch_solve_batch(const BatchJob* jobs, int njobs, const int2* grp_rows,
                                int total_rows, const int2* grp_cols, int total_cols,
-                               size_t smem_rows, size_t smem_cols, int num_sms, cudaStream_t s,
-                               const cudaEvent_t* marks)
+                               size_t smem_rows, size_t smem_cols, int max_w, int num_sms,
+                               cudaStream_t s, const cudaEvent_t* marks)
 {
     if (total_rows <= 0) return cudaSuccess;
     const int thr = 256;
-    int occ_r = 0, occ_c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, k2_batch, thr, smem_rows);
+    // staged row drivers when their buffers (sized for the widest row) fit
+    const int Wp = (int)row_floats(max_w);
+    const size_t sm2 = sizeof(float) * 5 * (size_t)Wp + smem_rows;
+    const size_t sm4 = align16(sizeof(float2) * 2 * (size_t)(Wp / 2 + 1)) + sizeof(float) * 2 * (size_t)Wp + smem_rows;
+    const bool staged = sm2 <= kSmemCap && sm4 <= kSmemCap;
+    int occ_r = 0, occ_c = 0, occ_2 = 0, occ_4 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k3_batch, thr, smem_cols);
-    const int grid_r = std::max(1, std::min(total_rows, num_sms * std::max(occ_r, 1)));
     const int grid_c = std::max(1, std::min(total_cols, num_sms * std::max(occ_c, 1)));
-    k2_batch<<<grid_r, thr, smem_rows, s>>>(jobs, grp_rows, njobs, total_rows);
+    if (staged) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_2, k2_batch_staged, kStagedThreads, sm2);
+        const int grid_2 = std::max(1, std::min(total_rows, num_sms * std::max(occ_2, 1)));
+        k2_batch_staged<<<grid_2, kStagedThreads, sm2, s>>>(jobs, grp_rows, njobs, total_rows, Wp);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, k2_batch, thr, smem_rows);
+        const int grid_r = std::max(1, std::min(total_rows, num_sms * std::max(occ_r, 1)));
+        k2_batch<<<grid_r, thr, smem_rows, s>>>(jobs, grp_rows, njobs, total_rows);
+    }
     if (marks) cudaEventRecord(marks[0], s);
     k3_batch<<<grid_c, thr, smem_cols, s>>>(jobs, grp_cols, njobs, total_cols);
     if (marks) cudaEventRecord(marks[1], s);
-    k4_batch<<<grid_r, thr, smem_rows, s>>>(jobs, grp_rows, njobs, total_rows);
+    if (staged) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_4, k4_batch_staged, kStagedThreads, sm4);
+        const int grid_4 = std::max(1, std::min(total_rows, num_sms * std::max(occ_4, 1)));
+        k4_batch_staged<<<grid_4, kStagedThreads, sm4, s>>>(jobs, grp_rows, njobs, total_rows, Wp);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, k4_batch, thr, smem_rows);
+        const int grid_r = std::max(1, std::min(total_rows, num_sms * std::max(occ_r, 1)));
+        k4_batch<<<grid_r, thr, smem_rows, s>>>(jobs, grp_rows, njobs, total_rows);
+    }
     return cudaGetLastError();
 }
 
