@@ -196,7 +196,7 @@ static cudaError_t blf_launch(blfls_handle* h, const float* img, float* ex, floa
 // K2-K4 on one channel with optional timing.
 static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex, const float* ey,
                                 float* out, const FftPlanDev& rp, const FftPlanDev& cp,
-                                const SolveParams& sp, cudaStream_t s)
+                                const SolveParams& sp, cudaStream_t s, float2* spec = nullptr)
 {
     const int a = prof_mark(h, s);
     cudaEvent_t marks[2];
@@ -208,7 +208,7 @@ static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex
         marks[0] = h->prof_pool[mi[0]];
         marks[1] = h->prof_pool[mi[1]];
     }
-    const cudaError_t e = launch_solve_residual(f, ex, ey, out, h->spec, rp, cp, rp.lap, cp.lap, sp,
+    const cudaError_t e = launch_solve_residual(f, ex, ey, out, spec ? spec : h->spec, rp, cp, rp.lap, cp.lap, sp,
                                                 s, h->num_sms, timed ? marks : nullptr);
     const int b = timed ? prof_mark(h, s) : -1;
     if (timed) {
@@ -221,19 +221,60 @@ static cudaError_t solve_launch(blfls_handle* h, const float* f, const float* ex
     return e;
 }
 
-// The passes of one channel (the channels of an image are filtered and solved independently).
+// The passes of one channel (the channels of an image are filtered and solved independently),
+// with the given residual planes and spectrum.
 static int run_channel(blfls_handle* h, const float* img, float* out, const BlfParams& bp,
                        const SolveParams& sp, const FftPlanDev& rp, const FftPlanDev& cp,
-                       int iters, cudaStream_t s)
+                       int iters, cudaStream_t s, float* ex = nullptr, float* ey = nullptr,
+                       float2* spec = nullptr)
 {
+    if (!ex) {
+        ex = h->ex;
+        ey = h->ey;
+    }
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
-        cudaError_t e = blf_launch(h, src, h->ex, h->ey, 1, bp, s);
+        cudaError_t e = blf_launch(h, src, ex, ey, 1, bp, s);
         if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
-        e = solve_launch(h, src, h->ex, h->ey, out, rp, cp, sp, s);
+        e = solve_launch(h, src, ex, ey, out, rp, cp, sp, s, spec);
         if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
     }
     return BLFLS_OK;
+}
+
+// Scratch and streams for running channels 1..C-1 beside channel 0.  Returns false (and the
+// caller runs the channels one after another) when the memory budget has no room for them.
+static bool ensure_channel_slots(blfls_handle* h, int C, size_t plane, size_t spec_elems)
+{
+    const size_t per = 2 * plane + 2 * spec_elems;   // ex, ey, then the spectrum as floats
+    const size_t need = per * (size_t)(C - 1);
+    if (need > h->chan_cap) {
+        const size_t old_bytes = h->chan_cap * sizeof(float), new_bytes = need * sizeof(float);
+        if (!budget_allows(h, new_bytes - std::min(old_bytes, new_bytes))) return false;
+        if (h->chan_scratch) cudaFree(h->chan_scratch);
+        h->used -= old_bytes;
+        h->chan_scratch = nullptr;
+        h->chan_cap = 0;
+        void* p = nullptr;
+        if (cudaMalloc(&p, new_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        h->chan_scratch = static_cast<float*>(p);
+        h->chan_cap = need;
+        h->used += new_bytes;
+    }
+    while ((int)h->chan_streams.size() < C - 1) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
+        h->chan_streams.push_back(st);
+    }
+    while ((int)h->chan_events.size() < C) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+        h->chan_events.push_back(ev);
+    }
+    return true;
 }
 
 int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
@@ -254,6 +295,34 @@ int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int 
     if (rc != BLFLS_OK) return rc;
     const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
     const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    const size_t spec_elems = (size_t)H * (W / 2 + 1);
+    // Channels on their own streams: one channel's latency-bound solve overlaps another
+    // channel's bilateral kernel.  Radii that use the shared gradient scratch run in order, and
+    // so does a profiled call (its per-kernel spans must not overlap).
+    if (C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
+        ensure_channel_slots(h, C, plane, spec_elems)) {
+        cudaEventRecord(h->chan_events[0], s);
+        for (int c = 1; c < C; ++c) cudaStreamWaitEvent(h->chan_streams[c - 1], h->chan_events[0], 0);
+        for (int c = 0; c < C; ++c) {
+            cudaStream_t sc = c == 0 ? s : h->chan_streams[c - 1];
+            float *ex = nullptr, *ey = nullptr;
+            float2* spec = nullptr;
+            if (c > 0) {
+                float* base = h->chan_scratch + (size_t)(c - 1) * (2 * plane + 2 * spec_elems);
+                ex = base;
+                ey = base + plane;
+                spec = reinterpret_cast<float2*>(base + 2 * plane);
+            }
+            if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, sc,
+                                  ex, ey, spec)) != BLFLS_OK)
+                return rc;
+        }
+        for (int c = 1; c < C; ++c) {
+            cudaEventRecord(h->chan_events[c], h->chan_streams[c - 1]);
+            cudaStreamWaitEvent(s, h->chan_events[c], 0);
+        }
+        return BLFLS_OK;
+    }
     for (int c = 0; c < C; ++c)
         if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
             return rc;
@@ -303,11 +372,25 @@ static int smooth_host_pipelined(blfls_handle* h, const float* img_host, float* 
         if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
         if ((e = cudaEventRecord(ev_in[c], cs)) != cudaSuccess) return cuda_fail(e, "event record");
     }
+    // Channels on their own streams (as in run_smooth) when the scratch fits and no profile runs.
+    const size_t spec_elems = (size_t)H * (W / 2 + 1);
+    const bool par = C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
+                     ensure_channel_slots(h, C, plane, spec_elems);
     for (int c = 0; c < C; ++c) {
-        if ((e = cudaStreamWaitEvent(s, ev_in[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
-        if ((rc = run_channel(h, dimg + c * plane, dout + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
+        cudaStream_t sc = (par && c > 0) ? h->chan_streams[c - 1] : s;
+        float *ex = nullptr, *ey = nullptr;
+        float2* spec = nullptr;
+        if (par && c > 0) {
+            float* base = h->chan_scratch + (size_t)(c - 1) * (2 * plane + 2 * spec_elems);
+            ex = base;
+            ey = base + plane;
+            spec = reinterpret_cast<float2*>(base + 2 * plane);
+        }
+        if ((e = cudaStreamWaitEvent(sc, ev_in[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+        if ((rc = run_channel(h, dimg + c * plane, dout + c * plane, bp, sp, *rp, *cp, iters, sc,
+                              ex, ey, spec)) != BLFLS_OK)
             return rc;
-        if ((e = cudaEventRecord(ev_done[c], s)) != cudaSuccess) return cuda_fail(e, "event record");
+        if ((e = cudaEventRecord(ev_done[c], sc)) != cudaSuccess) return cuda_fail(e, "event record");
         if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
         e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
                             cudaMemcpyDeviceToHost, cs);
@@ -371,6 +454,9 @@ void blfls_destroy(blfls_handle* h)
     if (h->grid_keys) cudaFree(h->grid_keys);
     if (h->grid_keys_host) cudaFreeHost(h->grid_keys_host);
     if (h->nc_scratch) cudaFree(h->nc_scratch);
+    if (h->chan_scratch) cudaFree(h->chan_scratch);
+    for (cudaStream_t st : h->chan_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : h->chan_events) cudaEventDestroy(ev);
     delete h;
 }
 

@@ -44,6 +44,12 @@ struct blfls_handle {
     int* grid_keys_host = nullptr;   // pinned, 4 * BLFLS_MAX_CHANNELS
     float* nc_scratch = nullptr;     // blfls_smooth_nc: gradients, transforms, two buffers
     size_t nc_cap = 0;
+    // blfls_smooth: channels 1..C-1 run on their own streams with their own residual planes and
+    // spectrum (channel 0 uses ex/ey/spec and the caller's stream)
+    float* chan_scratch = nullptr;
+    size_t chan_cap = 0;             // floats
+    std::vector<cudaStream_t> chan_streams;
+    std::vector<cudaEvent_t> chan_events;   // [0] fork, [1..] joins
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;
