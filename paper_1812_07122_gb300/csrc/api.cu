@@ -242,8 +242,10 @@ static int run_channel(blfls_handle* h, const float* img, float* out, const BlfP
     return BLFLS_OK;
 }
 
-// Scratch and streams for running channels 1..C-1 beside channel 0.  Returns false (and the
-// caller runs the channels one after another) when the memory budget has no room for them.
+// Scratch and streams for running the channels of an image side by side: channels 1..C-1 get
+// their own residual planes and spectrum (channel 0 uses the handle's), every channel its own
+// stream.  Returns false (and the caller runs the channels one after another on its stream)
+// when the memory budget has no room or a stream or event cannot be made.
 static bool ensure_channel_slots(blfls_handle* h, int C, size_t plane, size_t spec_elems)
 {
     const size_t per = 2 * plane + 2 * spec_elems;   // ex, ey, then the spectrum as floats
@@ -264,17 +266,52 @@ static bool ensure_channel_slots(blfls_handle* h, int C, size_t plane, size_t sp
         h->chan_cap = need;
         h->used += new_bytes;
     }
-    while ((int)h->chan_streams.size() < C - 1) {
+    while ((int)h->chan_streams.size() < C) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
         h->chan_streams.push_back(st);
     }
-    while ((int)h->chan_events.size() < C) {
+    while ((int)h->chan_done.size() < C) {
         cudaEvent_t ev;
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
-        h->chan_events.push_back(ev);
+        h->chan_done.push_back(ev);
     }
+    if (!h->chan_fork && cudaEventCreateWithFlags(&h->chan_fork, cudaEventDisableTiming) != cudaSuccess)
+        return false;
     return true;
+}
+
+// The passes of every channel side by side, each channel on its own stream (one channel's
+// latency-bound solve overlaps another channel's bilateral kernel); ordered after the work
+// queued on `s` before the call, and `s` waits for all of it.  `in_ready[c]`, when given, is an
+// event the channel's first kernel waits for; `done[c]` receives each channel's end.
+static int run_channels_concurrent(blfls_handle* h, const float* img, float* out, int C,
+                                   size_t plane, size_t spec_elems, const BlfParams& bp,
+                                   const SolveParams& sp, const FftPlanDev& rp,
+                                   const FftPlanDev& cp, int iters, cudaStream_t s,
+                                   const cudaEvent_t* in_ready, const cudaEvent_t* done)
+{
+    cudaEventRecord(h->chan_fork, s);
+    for (int c = 0; c < C; ++c) {
+        cudaStream_t sc = h->chan_streams[c];
+        cudaStreamWaitEvent(sc, h->chan_fork, 0);
+        if (in_ready) cudaStreamWaitEvent(sc, in_ready[c], 0);
+        float *ex = nullptr, *ey = nullptr;
+        float2* spec = nullptr;
+        if (c > 0) {
+            float* base = h->chan_scratch + (size_t)(c - 1) * (2 * plane + 2 * spec_elems);
+            ex = base;
+            ey = base + plane;
+            spec = reinterpret_cast<float2*>(base + 2 * plane);
+        }
+        const int rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, rp, cp, iters, sc,
+                                   ex, ey, spec);
+        if (rc != BLFLS_OK) return rc;
+        cudaEventRecord(h->chan_done[c], sc);
+        if (done) cudaEventRecord(done[c], sc);
+        cudaStreamWaitEvent(s, h->chan_done[c], 0);
+    }
+    return BLFLS_OK;
 }
 
 int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int W, int C,
@@ -296,33 +333,13 @@ int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int 
     const BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
     const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
     const size_t spec_elems = (size_t)H * (W / 2 + 1);
-    // Channels on their own streams: one channel's latency-bound solve overlaps another
-    // channel's bilateral kernel.  Radii that use the shared gradient scratch run in order, and
-    // so does a profiled call (its per-kernel spans must not overlap).
+    // Channels side by side: one channel's latency-bound solve overlaps another channel's
+    // bilateral kernel.  Radii that use the shared gradient scratch run in order, and so does a
+    // profiled call (its per-kernel spans must not overlap).
     if (C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
-        ensure_channel_slots(h, C, plane, spec_elems)) {
-        cudaEventRecord(h->chan_events[0], s);
-        for (int c = 1; c < C; ++c) cudaStreamWaitEvent(h->chan_streams[c - 1], h->chan_events[0], 0);
-        for (int c = 0; c < C; ++c) {
-            cudaStream_t sc = c == 0 ? s : h->chan_streams[c - 1];
-            float *ex = nullptr, *ey = nullptr;
-            float2* spec = nullptr;
-            if (c > 0) {
-                float* base = h->chan_scratch + (size_t)(c - 1) * (2 * plane + 2 * spec_elems);
-                ex = base;
-                ey = base + plane;
-                spec = reinterpret_cast<float2*>(base + 2 * plane);
-            }
-            if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, sc,
-                                  ex, ey, spec)) != BLFLS_OK)
-                return rc;
-        }
-        for (int c = 1; c < C; ++c) {
-            cudaEventRecord(h->chan_events[c], h->chan_streams[c - 1]);
-            cudaStreamWaitEvent(s, h->chan_events[c], 0);
-        }
-        return BLFLS_OK;
-    }
+        ensure_channel_slots(h, C, plane, spec_elems))
+        return run_channels_concurrent(h, img, out, C, plane, spec_elems, bp, sp, *rp, *cp, iters,
+                                       s, nullptr, nullptr);
     for (int c = 0; c < C; ++c)
         if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
             return rc;
@@ -372,29 +389,31 @@ static int smooth_host_pipelined(blfls_handle* h, const float* img_host, float* 
         if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
         if ((e = cudaEventRecord(ev_in[c], cs)) != cudaSuccess) return cuda_fail(e, "event record");
     }
-    // Channels on their own streams (as in run_smooth) when the scratch fits and no profile runs.
+    // Channels side by side (as in run_smooth) when the scratch fits and no profile runs.
     const size_t spec_elems = (size_t)H * (W / 2 + 1);
     const bool par = C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
                      ensure_channel_slots(h, C, plane, spec_elems);
-    for (int c = 0; c < C; ++c) {
-        cudaStream_t sc = (par && c > 0) ? h->chan_streams[c - 1] : s;
-        float *ex = nullptr, *ey = nullptr;
-        float2* spec = nullptr;
-        if (par && c > 0) {
-            float* base = h->chan_scratch + (size_t)(c - 1) * (2 * plane + 2 * spec_elems);
-            ex = base;
-            ey = base + plane;
-            spec = reinterpret_cast<float2*>(base + 2 * plane);
-        }
-        if ((e = cudaStreamWaitEvent(sc, ev_in[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
-        if ((rc = run_channel(h, dimg + c * plane, dout + c * plane, bp, sp, *rp, *cp, iters, sc,
-                              ex, ey, spec)) != BLFLS_OK)
+    if (par) {
+        if ((rc = run_channels_concurrent(h, dimg, dout, C, plane, spec_elems, bp, sp, *rp, *cp,
+                                          iters, s, ev_in, ev_done)) != BLFLS_OK)
             return rc;
-        if ((e = cudaEventRecord(ev_done[c], sc)) != cudaSuccess) return cuda_fail(e, "event record");
-        if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
-        e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
-                            cudaMemcpyDeviceToHost, cs);
-        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+        for (int c = 0; c < C; ++c) {
+            if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+            e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
+                                cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+        }
+    } else {
+        for (int c = 0; c < C; ++c) {
+            if ((e = cudaStreamWaitEvent(s, ev_in[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+            if ((rc = run_channel(h, dimg + c * plane, dout + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
+                return rc;
+            if ((e = cudaEventRecord(ev_done[c], s)) != cudaSuccess) return cuda_fail(e, "event record");
+            if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+            e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
+                                cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+        }
     }
     if ((e = cudaEventRecord(ev_fin, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev_fin, 0)) != cudaSuccess)
         return cuda_fail(e, "stream ordering");
@@ -456,7 +475,8 @@ void blfls_destroy(blfls_handle* h)
     if (h->nc_scratch) cudaFree(h->nc_scratch);
     if (h->chan_scratch) cudaFree(h->chan_scratch);
     for (cudaStream_t st : h->chan_streams) cudaStreamDestroy(st);
-    for (cudaEvent_t ev : h->chan_events) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->chan_done) cudaEventDestroy(ev);
+    if (h->chan_fork) cudaEventDestroy(h->chan_fork);
     delete h;
 }
 

@@ -48,8 +48,9 @@ struct blfls_handle {
     // spectrum (channel 0 uses ex/ey/spec and the caller's stream)
     float* chan_scratch = nullptr;
     size_t chan_cap = 0;             // floats
-    std::vector<cudaStream_t> chan_streams;
-    std::vector<cudaEvent_t> chan_events;   // [0] fork, [1..] joins
+    std::vector<cudaStream_t> chan_streams;   // one per channel
+    std::vector<cudaEvent_t> chan_done;       // one per channel
+    cudaEvent_t chan_fork = nullptr;
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> io_events;
