@@ -35,39 +35,39 @@ std::vector<int> dif_positions(int N, const std::vector<int>& radices)
 
 // Plain FP64 mixed-radix FFT for lengths whose prime factors are 2, 3, 5 and 7 (recursive
 // decimation in time: n = p m with p the smallest prime factor), forward sign exp(-2 pi i nk/N).
-void host_fft_smooth(std::vector<std::complex<double>>& a)
+// Roots come from one table of the L-th roots of unity (w_n^e = root[e L / n]), so a plan costs
+// L cosines and sines.  `tmp` is scratch of n elements.
+void fft_smooth_rec(std::complex<double>* a, size_t n, const std::vector<std::complex<double>>& root,
+                    size_t rstep, std::complex<double>* tmp)
 {
-    const size_t n = a.size();
     if (n <= 1) return;
-    size_t p = 0;
+    size_t p = n;
     for (size_t q : {2, 3, 5, 7})
         if (n % q == 0) { p = q; break; }
-    if (p == 0) {   // not 7-smooth: plain DFT (not reached by the plans built here)
-        std::vector<std::complex<double>> out(n);
-        for (size_t k = 0; k < n; ++k)
-            for (size_t t = 0; t < n; ++t) {
-                const double ang = -2.0 * kPi * double((k * t) % n) / double(n);
-                out[k] += a[t] * std::complex<double>(std::cos(ang), std::sin(ang));
-            }
-        a = out;
-        return;
-    }
     const size_t m = n / p;
-    std::vector<std::vector<std::complex<double>>> sub(p, std::vector<std::complex<double>>(m));
     for (size_t r = 0; r < p; ++r)
-        for (size_t t = 0; t < m; ++t) sub[r][t] = a[t * p + r];
-    for (size_t r = 0; r < p; ++r) host_fft_smooth(sub[r]);
+        for (size_t t = 0; t < m; ++t) tmp[r * m + t] = a[t * p + r];
+    for (size_t r = 0; r < p; ++r) fft_smooth_rec(tmp + r * m, m, root, rstep * p, a);
     // X[k + m q] = sum_r w_n^(r (k + m q)) S_r[k]
     for (size_t k = 0; k < m; ++k)
         for (size_t q = 0; q < p; ++q) {
             const size_t kk = k + m * q;
-            std::complex<double> acc = 0.0;
-            for (size_t r = 0; r < p; ++r) {
-                const double ang = -2.0 * kPi * double((r * kk) % n) / double(n);
-                acc += sub[r][k] * std::complex<double>(std::cos(ang), std::sin(ang));
-            }
+            std::complex<double> acc = tmp[k];
+            for (size_t r = 1; r < p; ++r) acc += root[((r * kk) % n) * rstep] * tmp[r * m + k];
             a[kk] = acc;
         }
+}
+
+void host_fft_smooth(std::vector<std::complex<double>>& a)
+{
+    const size_t n = a.size();
+    if (n <= 1) return;
+    std::vector<std::complex<double>> root(n), tmp(n);
+    for (size_t j = 0; j < n; ++j) {
+        const double ang = -2.0 * kPi * double(j) / double(n);
+        root[j] = std::complex<double>(std::cos(ang), std::sin(ang));
+    }
+    fft_smooth_rec(a.data(), n, root, 1, tmp.data());
 }
 
 // Work length of a Bluestein transform of length N: the smallest 7-smooth L >= 2N - 1 (the
