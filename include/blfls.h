@@ -304,8 +304,9 @@ int blfls_autotune(blfls_handle *h, int H, int W, int C, int radius, int prec,
 /* Measured throughput of the arithmetic pipes the bilateral kernels use (no counterpart in the
  * paper; measurement support for the roofline).  On `device`, writes up to n of: rates[0] FP32
  * FFMA results, [1] packed fma.f32x2 FP32 results, [2] MUFU ex2.f32 results, [3] ex2.f16x2 FP16
- * results, [4] ex2.bf16x2 BF16 results -- each per clock per SM, from clock64 cycle counts of
- * one fully occupied block per SM.  Synchronous; allocates (and frees) a few bytes of device
+ * results, [4] ex2.bf16x2 BF16 results, [5] packed fma.f16x2 FP16 results, [6] multiply-adds
+ * of mma.sync m16n8k16 (FP16 inputs, FP32 accumulators) -- each per clock per SM, from clock64
+ * cycle counts of one fully occupied block per SM.  Synchronous; allocates (and frees) a few bytes of device
  * memory.  Returns BLFLS_EINVAL for a bad device or rates == NULL. */
 int blfls_pipe_rates(int device, double *rates, int n);
 

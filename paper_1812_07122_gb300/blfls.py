@@ -300,13 +300,14 @@ def blfls_profile_end(h):
     return list(ms), list(n)
 
 
-PIPE_RATE_NAMES = ["ffma_f32", "ffma2_f32", "ex2_f32", "ex2_f16x2", "ex2_bf16x2"]
+PIPE_RATE_NAMES = ["ffma_f32", "ffma2_f32", "ex2_f32", "ex2_f16x2", "ex2_bf16x2", "hfma2_f16",
+                   "hmma_m16n8k16_mac"]
 
 
 def blfls_pipe_rates(device: int = 0) -> dict:
     """Results per clock per SM of each arithmetic pipe, measured on the device."""
-    r = (ctypes.c_double * 5)()
-    _check(load().blfls_pipe_rates(int(device), r, 5))
+    r = (ctypes.c_double * len(PIPE_RATE_NAMES))()
+    _check(load().blfls_pipe_rates(int(device), r, len(PIPE_RATE_NAMES)))
     return dict(zip(PIPE_RATE_NAMES, list(r)))
 
 

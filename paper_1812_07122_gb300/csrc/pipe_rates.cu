@@ -50,7 +50,16 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi)
     return r;
 }
 
-// OP: 0 FFMA, 1 FFMA2 (f32x2), 2 ex2 f32, 3 ex2 f16x2, 4 ex2 bf16x2
+__device__ __forceinline__ void mma16816(float (&d)[4], unsigned a, unsigned b)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
+                 "{%4, %4, %4, %4}, {%5, %5}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a), "r"(b));
+}
+
+// OP: 0 FFMA, 1 FFMA2 (f32x2), 2 ex2 f32, 3 ex2 f16x2, 4 ex2 bf16x2, 5 HFMA2 (f16x2),
+// 6 mma.sync m16n8k16 (f16 inputs, f32 accumulators)
 template <int OP>
 __global__ void __launch_bounds__(kThreads) pipe_probe(long long* cycles, float* sink, int iters)
 {
@@ -104,6 +113,28 @@ __global__ void __launch_bounds__(kThreads) pipe_probe(long long* cycles, float*
             }
 #pragma unroll
         for (int k = 0; k < kChains; ++k) acc += __low2float(*reinterpret_cast<__half2*>(&a[k]));
+    } else if constexpr (OP == 5) {
+        __half2 a[kChains];
+        const __half2 m = __floats2half2_rn(0.999f, 0.999f), c = __floats2half2_rn(1e-3f, 1e-3f);
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __floats2half2_rn(seed + 0.01f * k, seed);
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = __hfma2(a[k], m, c);
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) acc += __low2float(a[k]);
+    } else if constexpr (OP == 6) {
+        float d[kChains][4];
+        const __half2 ah = __floats2half2_rn(seed, 0.5f), bh = __floats2half2_rn(0.25f, -seed);
+        const unsigned a = *reinterpret_cast<const unsigned*>(&ah);
+        const unsigned b = *reinterpret_cast<const unsigned*>(&bh);
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0.f;
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) mma16816(d[k], a, b);
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) acc += d[k][0] + d[k][3];
     } else {
         unsigned a[kChains];
         const __nv_bfloat162 mb = __floats2bfloat162_rn(-0.5f, -0.5f);
@@ -141,7 +172,8 @@ double run_probe(int num_sms, long long* d_cycles, float* d_sink, int iters)
         return -1.0;
     std::sort(cyc.begin(), cyc.end());
     const double med = (double)cyc[num_sms / 2];
-    const double per_instr = (OP == 0 || OP == 2) ? 1.0 : 2.0;
+    // results per thread-instruction; an m16n8k16 MMA is 16 * 8 * 16 multiply-adds per warp
+    const double per_instr = (OP == 0 || OP == 2) ? 1.0 : OP == 6 ? 2048.0 / 32.0 : 2.0;
     return (double)kThreads * kChains * iters * per_instr / med;
 }
 
@@ -163,13 +195,15 @@ extern "C" int blfls_pipe_rates(int device, double* rates, int n)
         rc = BLFLS_ENOMEM;
     } else {
         const int iters = 2048;
-        double r[5];
+        double r[7];
         r[0] = run_probe<0>(num_sms, d_cycles, d_sink, iters);
         r[1] = run_probe<1>(num_sms, d_cycles, d_sink, iters);
         r[2] = run_probe<2>(num_sms, d_cycles, d_sink, iters / 4);
         r[3] = run_probe<3>(num_sms, d_cycles, d_sink, iters / 4);
         r[4] = run_probe<4>(num_sms, d_cycles, d_sink, iters / 4);
-        for (int i = 0; i < n && i < 5; ++i) rates[i] = r[i];
+        r[5] = run_probe<5>(num_sms, d_cycles, d_sink, iters);
+        r[6] = run_probe<6>(num_sms, d_cycles, d_sink, iters / 8);
+        for (int i = 0; i < n && i < 7; ++i) rates[i] = r[i];
         if (cudaGetLastError() != cudaSuccess) rc = BLFLS_ECUDA;
     }
     if (d_cycles) cudaFree(d_cycles);
