@@ -189,7 +189,9 @@ int blfls_smooth_grid(blfls_handle *h, const float *img, float *out, int H, int 
  * ct = running sum of 1 + (sigma_s / sigma_r) |g[j] - g[j-1]| along each row and each column
  * (periodic lines; computed once per pass from the unfiltered field), then nc_iters box
  * iterations of radius r_k = sigma_s sqrt(3) 2^(nc_iters-k) / sqrt(4^nc_iters - 1) sqrt(3) in the
- * transformed domain, rows then columns; then the Fourier solve of Eq. 8.  FP32.  Device
+ * transformed domain, rows then columns; then the Fourier solve of Eq. 8.  FP32 values; the
+ * transform is exact (FP32 steps capped at 2^20, summed as integers in units of 2^-23), so the
+ * set of samples in each box does not depend on rounding.  Device
  * pointers [C][H][W], async; out may equal img.  sigma_s in (0, BLFLS_MAX_NC_SIGMA_S]; sigma_r
  * > 0 (+inf: plain box iterations); nc_iters in [1, BLFLS_MAX_NC_ITERS] (3 is the usual choice).
  * Errors: BLFLS_EINVAL, BLFLS_ENOMEM, BLFLS_ECUDA. */

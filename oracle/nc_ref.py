@@ -20,11 +20,13 @@ once from the unfiltered field and used in every iteration; rows and columns are
 copy of a row one period to the right sits at ct + T, T = ct[W-1] + 1 + a |s[0] - s[W-1]|; N = 3
 by default.
 
-Which samples enter a box is decided by floating point, so the decision is taken in FP32 exactly
-as the CUDA kernels take it: FP32 gradients; increments 1 + a |ds| with a = sigma_s / sigma_r
-(FP32 division), one FP32 multiply and one add (no fused multiply-add); the running sum
-accumulated sequentially in FP32 along the line; r_k computed in FP64 and rounded to FP32; the
-test |(ct[j] + k T) - ct[i]| <= r_k in FP32.  The averaged values are FP64.
+Which samples enter a box must not depend on rounding order, so the transform is kept exact:
+FP32 gradients; each increment 1 + a |ds| with a = sigma_s / sigma_r (FP32 division) is one FP32
+multiply then one add (no fused multiply-add), capped at 2^20 (an increment beyond every box
+radius separates the samples either way, so no decision changes); an FP32 value >= 1 is a
+multiple of 2^-23, so ct and T are held exactly as integers in units of 2^-23 and summed in any
+order; r_k is computed in FP64 and rounded to FP32; the test |(ct[j] + k T) - ct[i]| <= r_k is
+then an exact comparison.  The averaged values are FP64.
 """
 from __future__ import annotations
 
@@ -34,6 +36,9 @@ import numpy as np
 
 from .blfls_ref import gradients, solve_eq8
 
+UNIT = 2 ** 23           # the transform is held in integer units of 2^-23
+INC_CAP = 2.0 ** 20      # increments are capped here (beyond every box radius)
+
 
 def nc_schedule(sigma_s: float, n_iter: int) -> list[float]:
     """Box radii r_k = sigma_k sqrt(3) of the N iterations (FP64)."""
@@ -42,29 +47,33 @@ def nc_schedule(sigma_s: float, n_iter: int) -> list[float]:
             for k in range(1, N + 1)]
 
 
+def _increments(s_hi: np.ndarray, s_lo: np.ndarray, a32: np.float32) -> np.ndarray:
+    """FP32 increments 1 + a |s_hi - s_lo| (multiply, then add), capped, as exact int64 units."""
+    d = np.float32(1.0) + a32 * np.abs(s_hi - s_lo)
+    d = np.minimum(d, np.float32(INC_CAP))
+    return (d.astype(np.float64) * UNIT).astype(np.int64)
+
+
 def domain_transform(s: np.ndarray, a, axis: int) -> tuple[np.ndarray, np.ndarray]:
-    """Periodic domain transform along `axis` in FP32 (see the module notes): ct (same shape)
-    and the period T (one per line)."""
+    """Periodic domain transform along `axis` (see the module notes): ct (same shape) and the
+    period T (one per line), both int64 in units of 2^-23."""
     s32 = np.moveaxis(np.asarray(s, dtype=np.float32), axis, -1)
     a32 = np.float32(a)
-    one = np.float32(1.0)
-    d = one + a32 * np.abs(s32[..., 1:] - s32[..., :-1])
-    ct = np.zeros(s32.shape, dtype=np.float32)
-    acc = np.zeros(s32.shape[:-1], dtype=np.float32)
-    for i in range(1, s32.shape[-1]):            # sequential FP32 running sum
-        acc = acc + d[..., i - 1]
-        ct[..., i] = acc
-    T = acc + (one + a32 * np.abs(s32[..., 0] - s32[..., -1]))
+    D = _increments(s32[..., 1:], s32[..., :-1], a32)
+    ct = np.zeros(s32.shape, dtype=np.int64)
+    ct[..., 1:] = np.cumsum(D, axis=-1)
+    T = ct[..., -1] + _increments(s32[..., 0], s32[..., -1], a32)
     return np.moveaxis(ct, -1, axis), T
 
 
 def nc_pass(v: np.ndarray, ct: np.ndarray, T: np.ndarray, r: float, axis: int) -> np.ndarray:
     """One normalised-convolution pass of radius r along `axis` with periodic lines; the
-    inclusion test in FP32 on the FP32 transform."""
+    inclusion test exact on the integer transform."""
     v = np.moveaxis(np.asarray(v, dtype=np.float64), axis, -1)
-    c = np.moveaxis(np.asarray(ct, dtype=np.float32), axis, -1)
-    T = np.asarray(T, dtype=np.float32)
+    c = np.moveaxis(np.asarray(ct, dtype=np.int64), axis, -1)
+    T = np.asarray(T, dtype=np.int64)
     r32 = np.float32(r)
+    r_units = int(math.floor(float(r32) * UNIT))   # |L| <= r  <=>  |L| <= floor(r 2^23) for integer L
     n = v.shape[-1]
     R = int(math.floor(r32))        # ct grows by >= 1 per sample, so |i - j| <= r
     acc = np.zeros_like(v)
@@ -74,8 +83,8 @@ def nc_pass(v: np.ndarray, ct: np.ndarray, T: np.ndarray, r: float, axis: int) -
         j = idx + d
         wraps = np.floor_divide(j, n)              # which period the neighbour sits in
         jm = j - wraps * n
-        cj = c[..., jm] + wraps.astype(np.float32) * T[..., None]
-        inside = np.abs(cj - c) <= r32
+        cj = c[..., jm] + wraps * T[..., None]
+        inside = np.abs(cj - c) <= r_units
         acc += np.where(inside, v[..., jm], 0.0)
         cnt += inside
     return np.moveaxis(acc / cnt, -1, axis)

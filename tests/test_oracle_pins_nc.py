@@ -23,22 +23,42 @@ def test_schedule_variances_sum_to_sigma_s_squared_and_halve():
 def test_domain_transform_by_hand():
     s = np.array([[0.0, 0.5, 0.5, 0.25]])
     ct, T = oracle.domain_transform(s, 2.0, axis=1)
-    # increments 1 + 2 |ds|: 2.0, 1.0, 1.5; wrap increment 1 + 2 |0 - 0.25| = 1.5 (all exact)
-    np.testing.assert_array_equal(ct, [[0.0, 2.0, 3.0, 4.5]])
-    np.testing.assert_array_equal(T, [6.0])
+    # increments 1 + 2 |ds|: 2.0, 1.0, 1.5; wrap increment 1 + 2 |0 - 0.25| = 1.5 (all exact),
+    # held in integer units of 2^-23
+    np.testing.assert_array_equal(ct, np.array([[0.0, 2.0, 3.0, 4.5]]) * 2 ** 23)
+    np.testing.assert_array_equal(T, [6 * 2 ** 23])
+
+
+def test_domain_transform_is_the_exact_running_sum():
+    """Against exact rational arithmetic (Python fractions of the FP32 increments): no rounding
+    in the sum, whatever its length, and the cap on one huge step."""
+    from fractions import Fraction
+    s = _rng(4).normal(scale=0.4, size=(3, 500)).astype(np.float32)
+    s[1, 200] = 1e6                                  # 1 + a |ds| far above the cap of 2^20
+    a = np.float32(62.5)
+    ct, T = oracle.domain_transform(s, a, axis=1)
+    for row in range(3):
+        acc = Fraction(0)
+        for i in range(1, 500):
+            d = min(np.float32(1.0) + a * np.float32(abs(s[row, i] - s[row, i - 1])),
+                    np.float32(2.0 ** 20))
+            acc += Fraction(float(d))
+            assert Fraction(int(ct[row, i]), 2 ** 23) == acc
+        d = min(np.float32(1.0) + a * np.float32(abs(s[row, 0] - s[row, -1])), np.float32(2.0 ** 20))
+        assert Fraction(int(T[row]), 2 ** 23) == acc + Fraction(float(d))
 
 
 def _nc_pass_brute(v, ct, T, r):
-    """Every sample of the previous, current and next period, scanned one by one (the FP32
-    inclusion test written out scalar by scalar)."""
+    """Every sample of the previous, current and next period, scanned one by one (the inclusion
+    test written out with Python's exact integer-float comparison)."""
     n = v.size
     out = np.empty(n)
-    r32 = np.float32(r)
+    r32 = float(np.float32(r))
     for i in range(n):
         acc = cnt = 0.0
         for k in (-1, 0, 1):
             for j in range(n):
-                if abs(np.float32(ct[j] + np.float32(k) * T) - ct[i]) <= r32:
+                if abs(int(ct[j]) + k * int(T) - int(ct[i])) <= r32 * 2 ** 23:
                     acc += v[j]
                     cnt += 1
         out[i] = acc / cnt
