@@ -157,11 +157,13 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
     if (LGC >= 0) lgc = LGC;
     fft_forward<LGC>(data, lgc, cp, tw);
     const int nfreq = cp.bluestein ? H : cp.L;
+    // every launch uses a multiple of 32 threads, so a thread's column i & (CB - 1) is the same
+    // in every iteration and its x eigenvalue is read once
+    const float sxv = __ldg(sx + min(kx0 + (int)(threadIdx.x & (CB - 1)), Wh - 1));
     for (int i = threadIdx.x; i < (nfreq << lgc); i += blockDim.x) {
-        const int p = i >> lgc, c = i & (CB - 1);
-        const int kx = min(kx0 + c, Wh - 1);
+        const int p = i >> lgc;
         const float syv = syp ? syp[p] : __ldg(sy + __ldg(cp.iperm + p));
-        const float den = fmaf(lam, __ldg(sx + kx) + syv, 1.0f);
+        const float den = fmaf(lam, sxv + syv, 1.0f);
         const float m = __fdividef(scale, den) * lam;
         const float2 v = data[i];
         data[i] = make_float2(v.x * m, v.y * m);
