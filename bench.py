@@ -17,7 +17,10 @@ the channels in order so that no other kernel overlaps a K1 launch), ``e2e`` (ho
 ``cpu_baseline`` (the FP64 oracle on the host cores, bounded sample, rank 0 at N=1 only) and
 ``forms`` (the FP16/BF16-weight precision forms on the same workload), ``modes`` (the LS model of
 Eq. 6, the detail-enhancement / log-tone applications of Section IV, joint and rolling-guidance
-smoothing of Section III-D, BLF-LS on the bilateral-grid filter, and NC-LS, on the same image).
+smoothing of Section III-D, BLF-LS on the bilateral-grid filter, and NC-LS, on the same image),
+``step_ms`` (median / p99 of the timed steps), ``small`` (the 256x256 grey workload, one pass),
+the batched and served forms, and, in ``cpu_baseline``, the oracle on one core and on the small
+workload.
 
 ``--impl reference`` times the FP64 oracle instead (the comparison arm; no GPU work).
 """
@@ -49,7 +52,7 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -57,6 +60,8 @@ def parse_args():
     ap.add_argument("--no-modes", action="store_true",
                     help="skip the LS-model and base/detail lines")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 256x256 workload line")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -391,8 +396,12 @@ def main():
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    step_times = sorted(a.elapsed_time(b) for a, b in ev)
+    total_ms = max_over_ranks(sum(step_times), dev)
     ms_per_step = total_ms / K
+    step_ms = {"median": round(statistics.median(step_times), 3),
+               "p99": round(step_times[min(K - 1, int(math.ceil(0.99 * K)) - 1)], 3),
+               "min": round(step_times[0], 3), "max": round(step_times[-1], 3)}
     mp = H * W / 1e6
     value = replica_throughput(mp, ms_per_step / 1e3, world)
 
@@ -524,6 +533,29 @@ def main():
     if not args.no_serve and rank == 0:
         serving = bench_serving(dev, args.serve_requests, args.serve_rate)
 
+    # the small grey workload (256x256, r 5, sigma_s 3, sigma_r 0.1, lambda 20, one pass) on the GPU
+    small = None
+    if not args.no_small and rank == 0:
+        fs = synth.image_256_rectangles()                # [1, 256, 256]
+        xs = torch.from_numpy(fs).to(dev)
+        ys = torch.empty_like(xs)
+        run_small = lambda: blfls.blfls_smooth(h, xs, ys, 256, 256, 1, 20.0, 3.0, 0.1, 5, 1, 0,
+                                               stream)
+        for _ in range(max(3, args.warmup)):
+            run_small()
+        torch.cuda.synchronize(dev)
+        n_small = max(50, K)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_small):
+            run_small()
+        b.record(stream)
+        b.synchronize()
+        small_ms = a.elapsed_time(b) / n_small
+        small = {"workload": "256x256 grey rectangles, radius 5, sigma_s 3, sigma_r 0.1, "
+                             "lambda 20, one pass, FP32 (back-to-back calls, inputs in L2)",
+                 "ms_per_call": round(small_ms, 4), "mp_per_s": round(0.065536 / small_ms * 1e3, 2)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -533,6 +565,22 @@ def main():
                "kind": "oracle",
                "sample": f"channel 0, one pass, whole 3840x2160 plane ({dt:.1f} s; "
                          f"{frac:.4f} of the workload), scaled to the whole workload"}
+        # one core, and the small grey workload on all cores and on one
+        dt1, frac1 = cpu_oracle_sample(f, 135, 1)
+        fs0 = synth.image_256_rectangles()[0]
+        t0 = time.perf_counter()
+        oracle.blfls_channel(fs0, 20.0, 3.0, 0.1, 5, threads)
+        c1_all = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.blfls_channel(fs0, 20.0, 3.0, 0.1, 5, 1)
+        c1_one = time.perf_counter() - t0
+        cpu["one_core"] = {"value": round(mp / (dt1 / frac1), 5), "unit": "MP/s", "cores": 1,
+                           "sample": f"channel 0, one pass, rows 0-134 ({dt1:.1f} s; "
+                                     f"{frac1:.5f} of the workload), scaled"}
+        cpu["small_workload"] = {"workload": "256x256 grey rectangles, radius 5, one pass",
+                                 "all_cores_s": round(c1_all, 3), "one_core_s": round(c1_one, 3),
+                                 "all_cores_mp_per_s": round(0.065536 / c1_all, 4),
+                                 "one_core_mp_per_s": round(0.065536 / c1_one, 4)}
 
     blfls.blfls_destroy(h)
     if rank == 0:
@@ -543,9 +591,9 @@ def main():
                 "config": {"workload": WORKLOAD, "H": H, "W": W, "C": C, **PARAMS,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "step_ms": step_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * K, "clocks": clocks, "forms": forms,
-                "modes": modes, "batched": batched, "serving": serving}
+                "modes": modes, "small": small, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
