@@ -18,6 +18,9 @@
 
 #include "internal.h"
 
+#include <type_traits>
+#include <utility>
+
 namespace blfls {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -487,6 +490,131 @@ __device__ __forceinline__ void fft_inverse(float2* x, int lgc, const FftPlanDev
 __device__ __forceinline__ unsigned row_pos(const FftPlanDev& p, unsigned q)
 {
     return p.pad_span ? q + __umulhi(q, p.pad_magic) : q;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Compile-time plans.  For the common lengths the radix sequence is a template argument, so the
+// butterfly spans, strides, twiddle steps, the divisions that locate a butterfly and the row
+// padding are all constants (shared-memory offsets become immediates, divisions become
+// multiply-shifts).  The arithmetic is the runtime plan's, operation for operation: the same
+// butterflies, twiddle-table entries and memory layout, so the results are bit-identical.
+// ---------------------------------------------------------------------------------------------
+template <int... Rs>
+struct CtPlan {
+    static constexpr int nst = sizeof...(Rs);
+    static constexpr int radix[nst] = {Rs...};
+    static constexpr int L = (Rs * ...);
+    static constexpr int span(int s)
+    {
+        int m = L;
+        for (int k = 0; k <= s; ++k) m /= radix[k];
+        return m;
+    }
+};
+
+template <int R> struct Bfly { using type = OneLevel<R>; };
+template <> struct Bfly<15> { using type = TwoLevel<3, 5>; };
+template <> struct Bfly<9> { using type = TwoLevel<3, 3>; };
+
+// One stage of a compile-time plan of length L: radix R, span M, column shift LGC, row padding
+// span PADS (0: none); INV selects the inverse (dit_inv_stage) form.
+template <int R, int M, int L, int LGC, int PADS, bool INV>
+__device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* __restrict__ tw)
+{
+    using B = typename Bfly<R>::type;
+    constexpr unsigned total = (unsigned)(L / R) << LGC;
+    constexpr unsigned mask = (1u << LGC) - 1u;
+    constexpr unsigned lblk = (unsigned)M * R;
+    constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : ((unsigned)M << LGC);
+    constexpr unsigned tw_step = (unsigned)(L / (M * R));
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned bi = b >> LGC;
+        const unsigned blk = bi / (unsigned)M;
+        const unsigned j = bi - blk * (unsigned)M;
+        unsigned base = blk * lblk + j;
+        if constexpr (PADS > 0) base += base / (unsigned)PADS;
+        float2* xb = x + ((base << LGC) + col);
+        float2 v[R];
+        if constexpr (!INV) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = xb[t * st];
+            B::template dft<false>(v);
+            if constexpr (M > 1) {
+                float2 w[R];
+                twiddle_powers<R, B::F>(w, tw, j * tw_step);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float2 y = v[B::slot(q)];
+                    xb[q * st] = q ? cmul(y, w[q]) : y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < R; ++q) xb[q * st] = v[B::slot(q)];
+            }
+        } else {
+            if constexpr (M > 1) {
+                float2 w[R];
+                twiddle_powers<R, B::F>(w, tw, j * tw_step);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float2 a = xb[q * st];
+                    v[q] = q ? cmulc(a, w[q]) : a;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[q] = xb[q * st];
+            }
+            B::template dft<true>(v);
+#pragma unroll
+            for (int t = 0; t < R; ++t) xb[t * st] = v[B::slot(t)];
+        }
+    }
+    __syncthreads();
+}
+
+template <class P, int LGC, int PADS, int... S>
+__device__ __forceinline__ void ct_forward_stages(float2* x, const float2* tw,
+                                                  std::integer_sequence<int, S...>)
+{
+    (ct_stage<P::radix[S], P::span(S), P::L, LGC, PADS, false>(x, tw), ...);
+}
+template <class P, int LGC, int PADS, int... S>
+__device__ __forceinline__ void ct_inverse_stages(float2* x, const float2* tw,
+                                                  std::integer_sequence<int, S...>)
+{
+    (ct_stage<P::radix[P::nst - 1 - S], P::span(P::nst - 1 - S), P::L, LGC, PADS, true>(x, tw), ...);
+}
+
+// Forward / unnormalised inverse DFT of every column with plan P (PAD: a padded row buffer,
+// lgc = 0; the padding span is L / radix[0] for plans of two or more stages).
+template <class P, int LGC, bool PAD>
+__device__ __forceinline__ void ct_forward(float2* x, const float2* tw)
+{
+    constexpr int PADS = (PAD && P::nst >= 2) ? P::L / P::radix[0] : 0;
+    ct_forward_stages<P, LGC, PADS>(x, tw, std::make_integer_sequence<int, P::nst>{});
+}
+template <class P, int LGC, bool PAD>
+__device__ __forceinline__ void ct_inverse(float2* x, const float2* tw)
+{
+    constexpr int PADS = (PAD && P::nst >= 2) ? P::L / P::radix[0] : 0;
+    ct_inverse_stages<P, LGC, PADS>(x, tw, std::make_integer_sequence<int, P::nst>{});
+}
+
+// Forward / inverse through plan P when it is a CtPlan, else through the runtime plan `p`.
+template <class P, int LGC, bool PAD>
+__device__ __forceinline__ void fft_forward_p(float2* x, int lgc, const FftPlanDev& p,
+                                              const float2* tw)
+{
+    if constexpr (std::is_void_v<P>) fft_forward<LGC, PAD>(x, lgc, p, tw);
+    else ct_forward<P, LGC, PAD>(x, tw);
+}
+template <class P, int LGC, bool PAD>
+__device__ __forceinline__ void fft_inverse_p(float2* x, int lgc, const FftPlanDev& p,
+                                              const float2* tw)
+{
+    if constexpr (std::is_void_v<P>) fft_inverse<LGC, PAD>(x, lgc, p, tw);
+    else ct_inverse<P, LGC, PAD>(x, tw);
 }
 
 }  // namespace blfls

@@ -99,11 +99,13 @@ __device__ __forceinline__ void k2_build(const float* ex0, const float* ex1, con
 }
 
 // K2, second half: forward FFT of z, split into the two half spectra s0, s1 (W/2+1 bins each).
+// P: a compile-time plan matching rp, or void.
+template <class P = void>
 __device__ __forceinline__ void k2_transform(bool has1, int W, float2* s0, float2* s1,
                                              const FftPlanDev& rp, const float2* tw, float2* data)
 {
     const int Wh = W / 2 + 1;
-    fft_forward<0, true>(data, 0, rp, tw);
+    fft_forward_p<P, 0, true>(data, 0, rp, tw);
 #pragma unroll 4
     for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
         const int kn = (k == 0) ? 0 : W - k;
@@ -144,8 +146,9 @@ __device__ __forceinline__ void k2_item(const float* __restrict__ ex, const floa
 // K3 on one column block already in `data` (rows n < H; the caller synchronised): forward FFT
 // down the columns, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the 1/(HW) of the
 // inverse), inverse FFT.  Ends synchronised.
-template <int LGC = -1>
 // `syp`, when given, holds sy[iperm[p]] for every work position p (staged once per CTA).
+// P: a compile-time plan matching cp, or void.
+template <int LGC = -1, class P = void>
 __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int kx0, int lgc,
                                                const FftPlanDev& cp, const float* __restrict__ sx,
                                                const float* __restrict__ sy, float lam,
@@ -155,7 +158,7 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
     const int CB = 1 << lgc;
     const int Wh = W / 2 + 1;
     if (LGC >= 0) lgc = LGC;
-    fft_forward<LGC>(data, lgc, cp, tw);
+    fft_forward_p<P, LGC, false>(data, lgc, cp, tw);
     const int nfreq = cp.bluestein ? H : cp.L;
     // every launch uses a multiple of 32 threads, so a thread's column i & (CB - 1) is the same
     // in every iteration and its x eigenvalue is read once
@@ -169,7 +172,7 @@ __device__ __forceinline__ void k3_solve_block(float2* data, int H, int W, int k
         data[i] = make_float2(v.x * m, v.y * m);
     }
     __syncthreads();
-    fft_inverse<LGC>(data, lgc, cp, tw);
+    fft_inverse_p<P, LGC, false>(data, lgc, cp, tw);
 }
 
 // K3: columns [blk * 2^lgc, (blk + 1) * 2^lgc) of the half spectrum of one channel.
@@ -377,6 +380,7 @@ __host__ __device__ __forceinline__ size_t k3s_smem(int L, int lgc)
            sizeof(float) * (size_t)L;
 }
 
+template <class P>
 __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float* __restrict__ ex,
                                                                     const float* __restrict__ ey,
                                                                     float2* __restrict__ spec,
@@ -412,11 +416,12 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_staged(const float*
         const bool has1 = y1 < H;
         k2_build(st, st + Wp, st + 2 * Wp, st + 3 * Wp, st + 4 * Wp, has1, W, rp, data);
         if (p + 1 < p1) issue(p + 1);   // the rows of pair p have been read out
-        k2_transform(has1, W, spec + (size_t)y0 * Wh, spec + (size_t)(has1 ? y1 : y0) * Wh, rp,
-                     rp.tw, data);
+        k2_transform<P>(has1, W, spec + (size_t)y0 * Wh, spec + (size_t)(has1 ? y1 : y0) * Wh,
+                        rp, rp.tw, data);
     }
 }
 
+template <class P>
 __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2* __restrict__ spec,
                                                                     const float* f, float* out,
                                                                     int H, int W, FftPlanDev rp,
@@ -455,7 +460,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
         k4_rebuild(ss, ss + Wh, has1, W, rp, data);
         const bool more = p + 1 < p1;
         if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
-        fft_inverse<0, true>(data, 0, rp, rp.tw);
+        fft_inverse_p<P, 0, true>(data, 0, rp, rp.tw);
         if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
         __syncthreads();
         k4_output(has1, sf, sf + Wp, out + (size_t)y0 * W, out + (size_t)(has1 ? y1 : y0) * W, W,
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
 // Launched with any block size up to kColThreadsMax (chosen per plan, see col_threads).
 constexpr int kColThreadsMax = 576;
 
-template <int LGC>
+template <int LGC, class P>
 __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restrict__ spec, int H,
                                                                  int W, FftPlanDev cp,
                                                                  const float* __restrict__ sx,
@@ -512,7 +517,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restr
         }
         __syncthreads();
         const int kx0 = b * CB;
-        k3_solve_block<LGC>(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tws, syp);
+        k3_solve_block<LGC, P>(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tws, syp);
         for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
             const int n = i >> lgc, c = i & (CB - 1);
             const int kx = kx0 + c;
@@ -730,6 +735,8 @@ int threads_for(int work)
 
 }  // namespace
 
+static void set_staged_attributes();   // below, with the plan pickers
+
 void init_solve_kernel_attributes()
 {
     cudaFuncSetAttribute(k2_rows_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -738,13 +745,7 @@ void init_solve_kernel_attributes()
     cudaFuncSetAttribute(k2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k3_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k2_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k3_cols_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k4_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    set_staged_attributes();
     cudaFuncSetAttribute(k2_batch_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k4_batch_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
@@ -777,15 +778,67 @@ int solve_fit_lgc(int L, int col_block)
 // kColThreadsMax) with the least sum over stages of ceil(butterflies / threads) divided by the
 // number of CTAs that fit on an SM.
 typedef void (*ColsStagedFn)(float2*, int, int, FftPlanDev, const float*, const float*, float, float);
-static ColsStagedFn cols_staged_kernel(int lgc)
+typedef void (*RowsK2Fn)(const float*, const float*, float2*, int, int, FftPlanDev, int);
+typedef void (*RowsK4Fn)(const float2*, const float*, float*, int, int, FftPlanDev, int);
+
+// Compile-time plans of the staged drivers: row lengths 3840 and 1920, column lengths 2160 and
+// 1080 (the radix sequences factor_direct gives them); other lengths use the runtime plan.
+using RowPlanA = CtPlan<16, 16, 15>;   // 3840
+using RowPlanB = CtPlan<16, 8, 15>;    // 1920
+using ColPlanA = CtPlan<16, 15, 9>;    // 2160
+using ColPlanB = CtPlan<8, 15, 9>;     // 1080
+
+template <class P>
+static bool plan_is(const FftPlanDev& p)
+{
+    if (p.bluestein || p.nst != P::nst || p.L != P::L) return false;
+    for (int s = 0; s < P::nst; ++s)
+        if (p.radix[s] != P::radix[s]) return false;
+    return true;
+}
+
+static RowsK2Fn rows_k2_kernel(const FftPlanDev& rp)
+{
+    if (plan_is<RowPlanA>(rp)) return k2_rows_staged<RowPlanA>;
+    if (plan_is<RowPlanB>(rp)) return k2_rows_staged<RowPlanB>;
+    return k2_rows_staged<void>;
+}
+static RowsK4Fn rows_k4_kernel(const FftPlanDev& rp)
+{
+    if (plan_is<RowPlanA>(rp)) return k4_rows_staged<RowPlanA>;
+    if (plan_is<RowPlanB>(rp)) return k4_rows_staged<RowPlanB>;
+    return k4_rows_staged<void>;
+}
+
+template <class P>
+static ColsStagedFn cols_staged_kernel_p(int lgc)
 {
     switch (lgc) {
-        case 0: return k3_cols_staged<0>;
-        case 1: return k3_cols_staged<1>;
-        case 2: return k3_cols_staged<2>;
-        case 3: return k3_cols_staged<3>;
-        default: return k3_cols_staged<4>;   // col_block is at most 16
+        case 0: return k3_cols_staged<0, P>;
+        case 1: return k3_cols_staged<1, P>;
+        case 2: return k3_cols_staged<2, P>;
+        case 3: return k3_cols_staged<3, P>;
+        default: return k3_cols_staged<4, P>;   // col_block is at most 16
     }
+}
+static ColsStagedFn cols_staged_kernel(int lgc, const FftPlanDev& cp)
+{
+    if (plan_is<ColPlanA>(cp)) return cols_staged_kernel_p<ColPlanA>(lgc);
+    if (plan_is<ColPlanB>(cp)) return cols_staged_kernel_p<ColPlanB>(lgc);
+    return cols_staged_kernel_p<void>(lgc);
+}
+
+static void set_staged_attributes()
+{
+    const int big = 227 * 1024;
+    for (RowsK2Fn f : {k2_rows_staged<void>, k2_rows_staged<RowPlanA>, k2_rows_staged<RowPlanB>})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    for (RowsK4Fn f : {k4_rows_staged<void>, k4_rows_staged<RowPlanA>, k4_rows_staged<RowPlanB>})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    for (int lgc = 0; lgc <= 4; ++lgc)
+        for (ColsStagedFn f : {cols_staged_kernel_p<void>(lgc), cols_staged_kernel_p<ColPlanA>(lgc),
+                               cols_staged_kernel_p<ColPlanB>(lgc)})
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 static int col_threads(const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
@@ -794,7 +847,7 @@ static int col_threads(const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
     double best = 1e30;
     for (int t = 128; t <= kColThreadsMax; t += 32) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cols_staged_kernel(lgc), t, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cols_staged_kernel(lgc, cp), t, smem);
         if (occ < 1) continue;
         long rounds = 0;
         for (int st = 0; st < cp.nst; ++st) {
@@ -831,9 +884,10 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     if (rows_staged) {
         const size_t sm2 = k2s_smem(W, rp);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_rows_staged, kStagedThreads, sm2);
+        const RowsK2Fn k2 = rows_k2_kernel(rp);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2, kStagedThreads, sm2);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
-        k2_rows_staged<<<grid, kStagedThreads, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
+        k2<<<grid, kStagedThreads, sm2, s>>>(ex, ey, spec, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
         const int tw_r = smem_r > sizeof(float2) * row_buf_elems(rp);
@@ -849,7 +903,7 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
         int occ = 0;
         const int thr = col_threads(cp, lgc, sm3, &occ);
         const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
-        cols_staged_kernel(lgc)<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
+        cols_staged_kernel(lgc, cp)<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
     } else {
         const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
         const int CB1 = 1 << lgc1;
@@ -866,9 +920,10 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     if (rows_staged) {
         const size_t sm4 = k4s_smem(W, rp);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_rows_staged, kStagedThreads, sm4);
+        const RowsK4Fn k4 = rows_k4_kernel(rp);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4, kStagedThreads, sm4);
         const int grid = std::max(1, std::min(npairs, num_sms * std::max(occ, 1)));
-        k4_rows_staged<<<grid, kStagedThreads, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
+        k4<<<grid, kStagedThreads, sm4, s>>>(spec, f, out, H, W, rp, al16 ? 1 : 0);
     } else {
         const size_t smem_r = solve_smem_rows(rp);
         const int tw_r = smem_r > sizeof(float2) * row_buf_elems(rp);

@@ -61,7 +61,8 @@ def test_blf_residual_matches_oracle(h, H, W, C, r, ss, sr):
 # Step 2: Fourier solve given residuals (oracle residuals in, so the solve is tested alone)
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("H,W", [(256, 256), (30, 50), (97, 61), (1, 64), (64, 1), (3, 5),
-                                 (2160, 3840), (1536, 2048), (211, 4096), (4093, 17)])
+                                 (2160, 3840), (1536, 2048), (211, 4096), (4093, 17),
+                                 (1080, 1920), (1080, 3840), (3840, 2160)])
 @pytest.mark.parametrize("lam", [0.0, 20.0, 1024.0])
 def test_solve_residual_matches_eq8(h, H, W, lam):
     rng = np.random.default_rng(H + 3 * W)
