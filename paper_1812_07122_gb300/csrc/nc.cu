@@ -1,25 +1,31 @@
 // NC-LS (Section III-D): BLF-LS with the bilateral filter replaced by the normalised convolution
 // of the domain transform.  Per channel and gradient field g (the periodic forward difference of
-// the image along x or y), with a = sigma_s / sigma_r:
-//   k8_grad      g for both fields;
-//   k8_dt_rows   ct_h[y][x] = sum_{x' = 1..x} (1 + a |g[y][x'] - g[y][x'-1]|) and the row period
-//                T_h[y] = ct_h[y][W-1] + 1 + a |g[y][0] - g[y][W-1]|: one CTA per row, a block scan
-//                over 2048-sample chunks staged in shared memory;
-//   k8_dt_cols   the same down every column: a CTA per 32 columns, each warp one segment of rows
-//                (segment totals first, then the segments re-scanned from their offsets);
-//   k8_nc_rows / k8_nc_cols  one box pass of radius r: the mean of the samples j of the periodic
-//                line with |(ct[j] + k T) - ct[i]| <= r (k = the period of j; a contiguous run
-//                around i), tiles staged in shared memory and one thread per strip of 8 samples
-//                holding the strip and its neighbourhood in registers, N iterations with
-//                r_k = sigma_s sqrt(3) 2^(N-k) / sqrt(4^N - 1) sqrt(3), rows then columns; the last
-//                column pass writes the residual e = v - g for the Fourier solve.
-// The transform is exact, so which samples enter a box does not depend on the summation order:
-// an increment is one FP32 multiply then one add (no fused multiply-add), capped at 2^20 (beyond
-// every box radius, so no decision changes); being an FP32 value >= 1 it is a multiple of 2^-23,
-// and ct and T are held as 64-bit integers in units of 2^-23 (at most 2^43 per step, 2^56 per
-// line); the box test is an integer comparison against floor(r 2^23).
+// the image along x or y), with a = sigma_s / sigma_r, the transform of a periodic line is the
+// running sum ct[i] = sum_{j=1..i} (1 + a |g[j] - g[j-1]|), and one box pass of radius r averages,
+// for every sample i, the samples j with |ct(j) - ct(i)| <= r (the line's copies one period over
+// shifted by the period T).  Since the transform grows by at least 1 per sample, those samples
+// form one run around i, and ct(j) - ct(i) is the sum of the steps between i and j: the box
+// passes need only the steps, never ct itself.
+//
+//   k8_grad_steps  the two fields and, for each field, its steps along x and along y;
+//   k8_nc_rows_strip / k8_nc_cols_strip  one box pass of radius r along rows / columns for
+//                R = floor(r) <= 16: a thread takes a strip of 8 samples, holds the strip and R_max
+//                neighbours on either side (values and steps) in registers, forms the running
+//                sum of the steps over that window and scans each sample's run outward (rows are
+//                staged through shared memory);
+//   k8_nc_rows / k8_nc_cols  larger radii: a sliding window per run of 32 samples;
+// N iterations with r_k = sigma_s sqrt(3) 2^(N-k) / sqrt(4^N - 1) sqrt(3), rows then columns; the
+// last column pass writes the residual e = v - g for the Fourier solve.
+//
+// Exactness: a step is one FP32 multiply then one add (no fused multiply-add), capped at 2^20;
+// an FP32 value >= 1 is a multiple of 2^-23, so a step is an integer number of 2^-23 units and
+// sums of steps are exact in 64-bit integers in any order.  Steps are stored as 32-bit units
+// clamped to rq_1 + 1 (rq = floor(r 2^23), rq_1 that of the first, widest iteration): a run
+// containing a clamped step exceeds every radius either way, so no box decision changes.  The
+// box test is an integer comparison.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "internal.h"
 
@@ -30,237 +36,66 @@ namespace {
 constexpr int kNcThreads = 256;
 constexpr float kIncCap = 1048576.0f;      // 2^20
 constexpr float kUnit = 8388608.0f;        // 2^23
-constexpr int kDtPer = 8;                  // row scan: samples per thread
-constexpr int kDtChunk = kNcThreads * kDtPer;
-constexpr int kColSegs = 32;               // column scan: row segments (warps) per CTA
 
-__global__ void __launch_bounds__(kNcThreads) k8_grad(const float* __restrict__ f,
-                                                     float* __restrict__ gx,
-                                                     float* __restrict__ gy, int H, int W)
+// One step in units of 2^-23, clamped to `clamp` (exact: v 2^23 is an integer below 2^44).
+__device__ __forceinline__ unsigned step_units(float a, float cur, float prev,
+                                               unsigned long long clamp)
+{
+    const float v = fminf(__fadd_rn(1.0f, __fmul_rn(a, fabsf(cur - prev))), kIncCap);
+    const unsigned long long u = (unsigned long long)__float2ll_rz(v * kUnit);
+    return (unsigned)(u < clamp ? u : clamp);
+}
+
+// g for both fields, and the steps of each field: sh_* between (y, x-1) and (y, x), sv_*
+// between (y-1, x) and (y, x), periodic.
+__global__ void __launch_bounds__(kNcThreads) k8_grad_steps(const float* __restrict__ f,
+                                                           float* __restrict__ gx,
+                                                           float* __restrict__ gy,
+                                                           unsigned* __restrict__ shx,
+                                                           unsigned* __restrict__ svx,
+                                                           unsigned* __restrict__ shy,
+                                                           unsigned* __restrict__ svy, int H,
+                                                           int W, float a,
+                                                           unsigned long long clamp)
 {
     const size_t n = (size_t)H * W;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
-        const float c = f[i];
-        gx[i] = f[(size_t)y * W + (x + 1 == W ? 0 : x + 1)] - c;
-        gy[i] = f[(size_t)(y + 1 == H ? 0 : y + 1) * W + x] - c;
+        const int xl = x == 0 ? W - 1 : x - 1, xr = x + 1 == W ? 0 : x + 1;
+        const int yu = y == 0 ? H - 1 : y - 1, yd = y + 1 == H ? 0 : y + 1;
+        const float* r0 = f + (size_t)y * W;
+        const float* ru = f + (size_t)yu * W;
+        const float* rd = f + (size_t)yd * W;
+        const float c = r0[x];
+        const float gx0 = r0[xr] - c, gy0 = rd[x] - c;            // the fields at (y, x)
+        const float gxl = c - r0[xl], gyl = rd[xl] - r0[xl];      // at (y, x-1)
+        const float gxu = ru[xr] - ru[x], gyu = c - ru[x];        // at (y-1, x)
+        gx[i] = gx0;
+        gy[i] = gy0;
+        shx[i] = step_units(a, gx0, gxl, clamp);
+        svx[i] = step_units(a, gx0, gxu, clamp);
+        shy[i] = step_units(a, gy0, gyl, clamp);
+        svy[i] = step_units(a, gy0, gyu, clamp);
     }
 }
 
-// One step of the transform in units of 2^-23 (exact: v 2^23 is an integer below 2^44).
-__device__ __forceinline__ long long dt_inc(float a, float cur, float prev)
-{
-    const float v = fminf(__fadd_rn(1.0f, __fmul_rn(a, fabsf(cur - prev))), kIncCap);
-    return __float2ll_rz(v * kUnit);
-}
-
-// Exclusive block scan of one value per thread (kNcThreads threads); *total receives the sum.
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* warp_sums,
-                                                     long long* total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    long long inc = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const long long o = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += o;
-    }
-    if (lane == 31) warp_sums[w] = inc;
-    __syncthreads();
-    long long before = 0, all = 0;
-#pragma unroll
-    for (int k = 0; k < kNcThreads / 32; ++k) {
-        const long long s = warp_sums[k];
-        before += k < w ? s : 0;
-        all += s;
-    }
-    __syncthreads();   // warp_sums may be rewritten by the next call
-    *total = all;
-    return before + inc - v;
-}
-
-// padded shared-memory slots: conflict-free reads of 8 consecutive samples per thread
-__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-
-// One CTA per row.
-__global__ void __launch_bounds__(kNcThreads) k8_dt_rows(const float* __restrict__ g,
-                                                        long long* __restrict__ ct,
-                                                        long long* __restrict__ T, int H, int W,
-                                                        float a)
-{
-    __shared__ float sg[kDtChunk + kDtChunk / 32 + 1];
-    __shared__ long long sc[kDtChunk + kDtChunk / 16];
-    __shared__ long long warp_sums[kNcThreads / 32];
-    const int y = blockIdx.x;
-    const float* row = g + (size_t)y * W;
-    long long* crow = ct + (size_t)y * W;
-    long long carry = 0;
-    for (int x0 = 0; x0 < W; x0 += kDtChunk) {
-        const int n = min(kDtChunk, W - x0);
-        for (int i = threadIdx.x; i < n; i += kNcThreads) sg[pad32(i)] = row[x0 + i];
-        __syncthreads();
-        const int b = threadIdx.x * kDtPer;
-        long long loc[kDtPer];
-        long long sum = 0;
-        float prev = b == 0 ? (x0 > 0 ? row[x0 - 1] : 0.f) : sg[pad32(b - 1)];
-#pragma unroll
-        for (int k = 0; k < kDtPer; ++k) {
-            const int i = b + k;
-            const float cur = i < n ? sg[pad32(i)] : prev;
-            if (i < n && x0 + i > 0) sum += dt_inc(a, cur, prev);
-            loc[k] = sum;
-            prev = cur;
-        }
-        long long chunk_total;
-        const long long before = carry + block_excl_scan(sum, warp_sums, &chunk_total);
-#pragma unroll
-        for (int k = 0; k < kDtPer; ++k)
-            if (b + k < n) sc[pad16(b + k)] = before + loc[k];
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += kNcThreads) crow[x0 + i] = sc[pad16(i)];
-        carry += chunk_total;
-        __syncthreads();   // sg and sc are refilled by the next chunk
-    }
-    if (threadIdx.x == 0) T[y] = carry + dt_inc(a, row[0], row[W - 1]);
-}
-
-// A CTA per 32 columns; warp w takes rows [w S, (w + 1) S) of them, S = ceil(H / kColSegs).
-__global__ void __launch_bounds__(32 * kColSegs) k8_dt_cols(const float* __restrict__ g,
-                                                           long long* __restrict__ ct,
-                                                           long long* __restrict__ T, int H,
-                                                           int W, float a)
-{
-    __shared__ long long seg[kColSegs][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + lane;
-    const int S = (H + kColSegs - 1) / kColSegs;
-    const int y0 = w * S, y1 = min(H, y0 + S);
-    const bool live = x < W && y0 < y1;
-    const float* col = g + x;
-    long long sum = 0;
-    if (live) {
-        float prev = y0 > 0 ? col[(size_t)(y0 - 1) * W] : 0.f;
-#pragma unroll 16
-        for (int y = y0; y < y1; ++y) {
-            const float cur = col[(size_t)y * W];
-            if (y > 0) sum += dt_inc(a, cur, prev);
-            prev = cur;
-        }
-    }
-    seg[w][lane] = sum;
-    __syncthreads();
-    long long off = 0, total = 0;
-#pragma unroll
-    for (int k = 0; k < kColSegs; ++k) {
-        off += k < w ? seg[k][lane] : 0;
-        total += seg[k][lane];
-    }
-    if (live) {
-        float prev = y0 > 0 ? col[(size_t)(y0 - 1) * W] : 0.f;
-        long long acc = off;
-#pragma unroll 16
-        for (int y = y0; y < y1; ++y) {
-            const float cur = col[(size_t)y * W];
-            if (y > 0) acc += dt_inc(a, cur, prev);
-            ct[(size_t)y * W + x] = acc;
-            prev = cur;
-        }
-    }
-    if (w == 0 && x < W) T[x] = total + dt_inc(a, col[0], col[(size_t)(H - 1) * W]);
-}
-
-// Box means by a sliding window.  The transform grows by at least 1 per sample (strictly
-// increasing, copies of the line one period over shifted by T), so the samples j inside the box
-// of sample i, |ct(j) - ct(i)| <= r, form one run [lo(i), hi(i)] of the unwrapped line, and both
-// ends only move forward as i does.  A thread takes kNcRun consecutive samples of one line: it
-// finds the first sample's run by scanning outward, then for every next sample advances hi over
-// the samples that have come inside and lo past those that have left, keeping the run's sum
-// (Neumaier-compensated FP32) and count.  The set is exactly the per-sample test's; only the
-// order of the additions differs from summing the run afresh.
-constexpr int kNcRun = 32;
-
-struct LinePos {   // position p of the unwrapped line: index p mod n and the shift k T
-    int m;
-    long long shift;
-};
-
-__device__ __forceinline__ void step_fwd(LinePos& q, int n, long long Tp)
-{
-    if (++q.m == n) { q.m = 0; q.shift += Tp; }
-}
-__device__ __forceinline__ void step_back(LinePos& q, int n, long long Tp)
-{
-    if (--q.m < 0) { q.m = n - 1; q.shift -= Tp; }
-}
-
-__device__ __forceinline__ void nsum_add(float& s, float& comp, float x)
-{
-    const float t = __fadd_rn(s, x);
-    comp += fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
-    s = t;
-}
-
-// Samples [i0, i1) of one line (length n, element stride st): out = box mean, minus g when given.
-__device__ __forceinline__ void box_run(const long long* __restrict__ c,
-                                        const float* __restrict__ v, size_t st, int n,
-                                        long long Tp, long long rq, int i0, int i1,
-                                        float* __restrict__ out, const float* __restrict__ g)
-{
-    auto C = [&](const LinePos& q) { return c[(size_t)q.m * st] + q.shift; };
-    LinePos lo{i0, 0}, hi{i0, 0};
-    long long ci = c[(size_t)i0 * st];
-    float sum = v[(size_t)i0 * st], comp = 0.f;
-    int cnt = 1;
-    for (;;) {   // the first sample's run, upwards
-        LinePos nx = hi;
-        step_fwd(nx, n, Tp);
-        if (C(nx) - ci > rq) break;
-        hi = nx;
-        nsum_add(sum, comp, v[(size_t)hi.m * st]);
-        ++cnt;
-    }
-    for (;;) {   // and downwards
-        LinePos pv = lo;
-        step_back(pv, n, Tp);
-        if (ci - C(pv) > rq) break;
-        lo = pv;
-        nsum_add(sum, comp, v[(size_t)lo.m * st]);
-        ++cnt;
-    }
-    for (int i = i0;;) {
-        const float m = (sum + comp) / (float)cnt;
-        out[(size_t)i * st] = g ? m - g[(size_t)i * st] : m;
-        if (++i >= i1) break;
-        ci = c[(size_t)i * st];
-        for (;;) {   // samples that have come inside at the top
-            LinePos nx = hi;
-            step_fwd(nx, n, Tp);
-            if (C(nx) - ci > rq) break;
-            hi = nx;
-            nsum_add(sum, comp, v[(size_t)hi.m * st]);
-            ++cnt;
-        }
-        while (ci - C(lo) > rq) {   // and those that have left at the bottom (lo <= i stays)
-            nsum_add(sum, comp, -v[(size_t)lo.m * st]);
-            --cnt;
-            step_fwd(lo, n, Tp);
-        }
-    }
-}
-
-// Box means for radii up to RM samples (R = floor(r) <= RM): a thread takes a strip of kNcStrip
-// consecutive samples of one line and holds the strip plus RM samples on either side in
-// registers (one load per sample instead of one per sample and neighbour); each sample's run is
-// then scanned outward over the registers, every comparison taken (predicated, no early exit).
+// ---------------------------------------------------------------------------------------------
+// Box means for R = floor(r) <= RM.  The window holds samples q = 0..NW-1 of the unwrapped line
+// (positions p0 + q): values vw[q] and steps sw[q] (the step into sample q; sw[0] unused).
+// ---------------------------------------------------------------------------------------------
 constexpr int kNcStrip = 8;
 
 template <int RM>
-__device__ __forceinline__ void strip_means(const long long (&cw)[kNcStrip + 2 * RM],
+__device__ __forceinline__ void strip_means(const unsigned (&sw)[kNcStrip + 2 * RM],
                                             const float (&vw)[kNcStrip + 2 * RM], long long rq,
                                             float (&mean)[kNcStrip])
 {
+    constexpr int NW = kNcStrip + 2 * RM;
+    long long cw[NW];   // running sum of the steps over the window (window-relative transform)
+    cw[0] = 0;
+#pragma unroll
+    for (int q = 1; q < NW; ++q) cw[q] = cw[q - 1] + (long long)sw[q];
 #pragma unroll
     for (int j = 0; j < kNcStrip; ++j) {
         const long long top = cw[RM + j] + rq, bottom = cw[RM + j] - rq;
@@ -277,24 +112,24 @@ __device__ __forceinline__ void strip_means(const long long (&cw)[kNcStrip + 2 *
     }
 }
 
-// Along x: a CTA stages a tile of 32 rows x 64 columns of the transform and the values, with RM
+// Along x: a CTA stages a tile of 32 rows x 64 columns of the values and the row steps, with RM
 // samples of periodic neighbourhood on either side, in shared memory with coalesced loads;
 // thread (lane, warp) takes row `lane` of the tile and a strip of kNcStrip columns (warp) and
 // reads the strip's window from shared memory (odd pitches put the lanes' rows in distinct
 // banks); the means go back through shared memory for coalesced stores.
 constexpr int kTileLong = kNcStrip * (kNcThreads / 32);   // 64 samples along the row
 constexpr int kTileWide = 32;                             // 32 rows
+
 template <int RM>
 __global__ void __launch_bounds__(kNcThreads) k8_nc_rows_strip(const float* __restrict__ v,
-                                                              const long long* __restrict__ ct,
-                                                              const long long* __restrict__ T,
+                                                              const unsigned* __restrict__ sh,
                                                               float* __restrict__ out, int H,
                                                               int W, long long rq)
 {
     constexpr int NW = kNcStrip + 2 * RM;
     constexpr int SPAN = kTileLong + 2 * RM;
     constexpr int PC = SPAN | 1, PO = kTileLong + 1;
-    __shared__ long long sc[kTileWide * PC];
+    __shared__ unsigned ss[kTileWide * PC];
     __shared__ float sv[kTileWide * PC];
     __shared__ float so[kTileWide * PO];
     const int tiles_x = (W + kTileLong - 1) / kTileLong;
@@ -303,27 +138,25 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_rows_strip(const float* __re
     for (int r = w; r < kTileWide; r += kNcThreads / 32) {
         const int y = y0 + r;
         if (y >= H) break;
-        const long long Ty = T[y];
         for (int q = lane; q < SPAN; q += 32) {
             int p = x0 - RM + q;                   // unwrapped column
-            long long sh = 0;
-            while (p < 0) { p += W; sh -= Ty; }
-            while (p >= W) { p -= W; sh += Ty; }
-            sc[r * PC + q] = ct[(size_t)y * W + p] + sh;
+            while (p < 0) p += W;
+            while (p >= W) p -= W;
+            ss[r * PC + q] = sh[(size_t)y * W + p];
             sv[r * PC + q] = v[(size_t)y * W + p];
         }
     }
     __syncthreads();
     if (y0 + lane < H) {
-        long long cw[NW];
+        unsigned sw[NW];
         float vw[NW];
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
-            cw[q] = sc[lane * PC + w * kNcStrip + q];
+            sw[q] = ss[lane * PC + w * kNcStrip + q];
             vw[q] = sv[lane * PC + w * kNcStrip + q];
         }
         float mean[kNcStrip];
-        strip_means<RM>(cw, vw, rq, mean);
+        strip_means<RM>(sw, vw, rq, mean);
 #pragma unroll
         for (int j = 0; j < kNcStrip; ++j) so[lane * PO + w * kNcStrip + j] = mean[j];
     }
@@ -342,8 +175,7 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_rows_strip(const float* __re
 // residual (mean - g).
 template <int RM>
 __global__ void __launch_bounds__(kNcThreads) k8_nc_cols_strip(const float* __restrict__ v,
-                                                              const long long* __restrict__ ct,
-                                                              const long long* __restrict__ T,
+                                                              const unsigned* __restrict__ svs,
                                                               float* __restrict__ out,
                                                               const float* __restrict__ g,
                                                               int H, int W, long long rq)
@@ -354,20 +186,18 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_cols_strip(const float* __re
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(t / W), x = (int)(t - (size_t)k * W);
-        const long long Tx = T[x];
         int m = k * kNcStrip - RM;
-        long long sh = 0;
-        while (m < 0) { m += H; sh -= Tx; }
-        long long cw[NW];
+        while (m < 0) m += H;
+        unsigned sw[NW];
         float vw[NW];
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
-            cw[q] = ct[(size_t)m * W + x] + sh;
+            sw[q] = svs[(size_t)m * W + x];
             vw[q] = v[(size_t)m * W + x];
-            if (++m == H) { m = 0; sh += Tx; }
+            if (++m == H) m = 0;
         }
         float mean[kNcStrip];
-        strip_means<RM>(cw, vw, rq, mean);
+        strip_means<RM>(sw, vw, rq, mean);
 #pragma unroll
         for (int j = 0; j < kNcStrip; ++j) {
             const int y = k * kNcStrip + j;
@@ -379,10 +209,87 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_cols_strip(const float* __re
     }
 }
 
-// Radii above the strip kernels: one thread per run of kNcRun samples with a sliding window.
+// ---------------------------------------------------------------------------------------------
+// Larger radii: a sliding window.  Both ends of a sample's run only move forward as the sample
+// does, so a thread takes kNcRun consecutive samples of one line, finds the first sample's run by
+// scanning outward, then for every next sample drops the samples that have left at the bottom and
+// adds those that have come inside at the top, keeping the run's sum (Neumaier-compensated FP32),
+// its count, and the transform distances from the current sample to both ends.
+// ---------------------------------------------------------------------------------------------
+constexpr int kNcRun = 32;
+
+__device__ __forceinline__ void nsum_add(float& s, float& comp, float x)
+{
+    const float t = __fadd_rn(s, x);
+    comp += fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
+    s = t;
+}
+
+// Samples [i0, i1) of one line (length n, element stride st); stp[p] is the step into sample p.
+__device__ __forceinline__ void box_run(const unsigned* __restrict__ stp,
+                                        const float* __restrict__ v, size_t st, int n,
+                                        long long rq, int i0, int i1, float* __restrict__ out,
+                                        const float* __restrict__ g)
+{
+    auto wrap = [n](int p) { return p >= n ? p - n : (p < 0 ? p + n : p); };
+    int lo = i0, hi = i0;                 // line indices of the run's ends (periodic)
+    long long dlo = 0, dhi = 0;           // transform distances from the sample to lo and to hi
+    float sum = v[(size_t)i0 * st], comp = 0.f;
+    int cnt = 1;
+    for (;;) {   // the first sample's run, upwards
+        const int nx = wrap(hi + 1);
+        const long long d = dhi + (long long)stp[(size_t)nx * st];
+        if (d > rq) break;
+        hi = nx;
+        dhi = d;
+        nsum_add(sum, comp, v[(size_t)hi * st]);
+        ++cnt;
+    }
+    for (;;) {   // and downwards
+        const long long d = dlo + (long long)stp[(size_t)lo * st];
+        if (d > rq) break;
+        lo = wrap(lo - 1);
+        dlo = d;
+        nsum_add(sum, comp, v[(size_t)lo * st]);
+        ++cnt;
+    }
+    for (int i = i0;;) {
+        const float m = (sum + comp) / (float)cnt;
+        out[(size_t)i * st] = g ? m - g[(size_t)i * st] : m;
+        if (++i >= i1) break;
+        if (dhi == 0) {   // the previous run ended at the previous sample: i starts a new run
+            lo = hi = i;
+            dlo = 0;
+            sum = v[(size_t)i * st];
+            comp = 0.f;
+            cnt = 1;
+        } else {          // i is inside the previous run
+            const long long step = stp[(size_t)i * st];
+            dhi -= step;
+            dlo += step;
+            while (dlo > rq) {   // samples that have left at the bottom
+                const int nl = wrap(lo + 1);
+                dlo -= (long long)stp[(size_t)nl * st];
+                nsum_add(sum, comp, -v[(size_t)lo * st]);
+                --cnt;
+                lo = nl;
+            }
+        }
+        for (;;) {   // samples that have come inside at the top
+            const int nx = wrap(hi + 1);
+            const long long d = dhi + (long long)stp[(size_t)nx * st];
+            if (d > rq) break;
+            hi = nx;
+            dhi = d;
+            nsum_add(sum, comp, v[(size_t)hi * st]);
+            ++cnt;
+        }
+    }
+}
+
+// Box pass along x: one thread per run of kNcRun samples of a row.
 __global__ void __launch_bounds__(kNcThreads) k8_nc_rows(const float* __restrict__ v,
-                                                        const long long* __restrict__ ct,
-                                                        const long long* __restrict__ T,
+                                                        const unsigned* __restrict__ sh,
                                                         float* __restrict__ out, int H, int W,
                                                         long long rq)
 {
@@ -392,14 +299,14 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_rows(const float* __restrict
          t += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(t / runs), k = (int)(t - (size_t)y * runs);
         const size_t row = (size_t)y * W;
-        box_run(ct + row, v + row, 1, W, T[y], rq, k * kNcRun, min(W, (k + 1) * kNcRun),
-                out + row, nullptr);
+        box_run(sh + row, v + row, 1, W, rq, k * kNcRun, min(W, (k + 1) * kNcRun), out + row,
+                nullptr);
     }
 }
 
+// Box pass along y: one thread per run of kNcRun samples of a column.
 __global__ void __launch_bounds__(kNcThreads) k8_nc_cols(const float* __restrict__ v,
-                                                        const long long* __restrict__ ct,
-                                                        const long long* __restrict__ T,
+                                                        const unsigned* __restrict__ svs,
                                                         float* __restrict__ out,
                                                         const float* __restrict__ g, int H,
                                                         int W, long long rq)
@@ -409,8 +316,8 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_cols(const float* __restrict
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(t / W), x = (int)(t - (size_t)k * W);
-        box_run(ct + x, v + x, (size_t)W, H, T[x], rq, k * kNcRun, min(H, (k + 1) * kNcRun),
-                out + x, g ? g + x : nullptr);
+        box_run(svs + x, v + x, (size_t)W, H, rq, k * kNcRun, min(H, (k + 1) * kNcRun), out + x,
+                g ? g + x : nullptr);
     }
 }
 
@@ -421,32 +328,31 @@ int nc_blocks(size_t n, int num_sms)
 }
 
 template <int RM>
-void box_pass_strips(const float* v, const long long* ct_h, const long long* T_h, float* mid,
-                     const long long* ct_v, const long long* T_v, float* out, const float* g,
-                     int H, int W, long long rq, int num_sms, cudaStream_t s)
+void box_pass_strips(const float* v, const unsigned* sh, float* mid, const unsigned* sv,
+                     float* out, const float* g, int H, int W, long long rq, int num_sms,
+                     cudaStream_t s)
 {
     const int row_tiles = ((H + kTileWide - 1) / kTileWide) * ((W + kTileLong - 1) / kTileLong);
-    k8_nc_rows_strip<RM><<<row_tiles, kNcThreads, 0, s>>>(v, ct_h, T_h, mid, H, W, rq);
+    k8_nc_rows_strip<RM><<<row_tiles, kNcThreads, 0, s>>>(v, sh, mid, H, W, rq);
     const size_t strips = (size_t)W * ((H + kNcStrip - 1) / kNcStrip);
-    k8_nc_cols_strip<RM><<<nc_blocks(strips, num_sms), kNcThreads, 0, s>>>(mid, ct_v, T_v, out, g,
-                                                                          H, W, rq);
+    k8_nc_cols_strip<RM><<<nc_blocks(strips, num_sms), kNcThreads, 0, s>>>(mid, sv, out, g, H, W,
+                                                                          rq);
 }
 
 // One iteration: box means along the rows of v into mid, then along the columns of mid into out
 // (minus g when given).  Strip kernels for R <= 16, sliding windows above.
-void nc_box_pass(const float* v, const long long* ct_h, const long long* T_h, float* mid,
-                 const long long* ct_v, const long long* T_v, float* out, const float* g, int H,
-                 int W, long long rq, int R, int num_sms, cudaStream_t s)
+void nc_box_pass(const float* v, const unsigned* sh, float* mid, const unsigned* sv, float* out,
+                 const float* g, int H, int W, long long rq, int R, int num_sms, cudaStream_t s)
 {
-    if (R <= 1) return box_pass_strips<1>(v, ct_h, T_h, mid, ct_v, T_v, out, g, H, W, rq, num_sms, s);
-    if (R <= 2) return box_pass_strips<2>(v, ct_h, T_h, mid, ct_v, T_v, out, g, H, W, rq, num_sms, s);
-    if (R <= 4) return box_pass_strips<4>(v, ct_h, T_h, mid, ct_v, T_v, out, g, H, W, rq, num_sms, s);
-    if (R <= 8) return box_pass_strips<8>(v, ct_h, T_h, mid, ct_v, T_v, out, g, H, W, rq, num_sms, s);
-    if (R <= 16) return box_pass_strips<16>(v, ct_h, T_h, mid, ct_v, T_v, out, g, H, W, rq, num_sms, s);
+    if (R <= 1) return box_pass_strips<1>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 2) return box_pass_strips<2>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 4) return box_pass_strips<4>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 8) return box_pass_strips<8>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 16) return box_pass_strips<16>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
     k8_nc_rows<<<nc_blocks((size_t)H * ((W + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(
-        v, ct_h, T_h, mid, H, W, rq);
+        v, sh, mid, H, W, rq);
     k8_nc_cols<<<nc_blocks((size_t)W * ((H + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(
-        mid, ct_v, T_v, out, g, H, W, rq);
+        mid, sv, out, g, H, W, rq);
 }
 
 }  // namespace
@@ -456,39 +362,42 @@ cudaError_t launch_nc_residuals(const float* f, float* ex, float* ey, int H, int
                                 cudaStream_t s, int num_sms)
 {
     const size_t plane = (size_t)H * W;
-    long long* ct_h = reinterpret_cast<long long*>(scratch);   // 8-byte aligned (device allocation)
-    long long* ct_v = ct_h + plane;
-    long long* T_h = ct_v + plane;
-    long long* T_v = T_h + H;
-    float* gx = reinterpret_cast<float*>(T_v + W);
+    float* gx = scratch;
     float* gy = gx + plane;
     float* va = gy + plane;
     float* vb = va + plane;
+    unsigned* shx = reinterpret_cast<unsigned*>(vb + plane);
+    unsigned* svx = shx + plane;
+    unsigned* shy = svx + plane;
+    unsigned* svy = shy + plane;
     const float a = std::isfinite(sigma_r) ? sigma_s / sigma_r : 0.0f;   // FP32 division
-    const int nb = nc_blocks(plane, num_sms);
-    k8_grad<<<nb, kNcThreads, 0, s>>>(f, gx, gy, H, W);
+    std::vector<float> r(n_iter);
+    for (int k = 1; k <= n_iter; ++k)
+        r[k - 1] = (float)((double)sigma_s * std::sqrt(3.0) * std::pow(2.0, n_iter - k) /
+                           std::sqrt(std::pow(4.0, n_iter) - 1.0) * std::sqrt(3.0));
+    const auto units = [](float rk) { return (long long)std::floor((double)rk * 8388608.0); };
+    // r_1 is the widest radius; sigma_s <= BLFLS_MAX_NC_SIGMA_S keeps rq_1 + 1 below 2^32
+    const unsigned long long clamp = (unsigned long long)units(r[0]) + 1;
+    if (clamp > 0xffffffffull) return cudaErrorInvalidValue;
+    k8_grad_steps<<<nc_blocks(plane, num_sms), kNcThreads, 0, s>>>(f, gx, gy, shx, svx, shy, svy,
+                                                                  H, W, a, clamp);
     for (int field = 0; field < 2; ++field) {
         const float* g = field == 0 ? gx : gy;
+        const unsigned* sh = field == 0 ? shx : shy;
+        const unsigned* sv = field == 0 ? svx : svy;
         float* e = field == 0 ? ex : ey;
-        k8_dt_rows<<<H, kNcThreads, 0, s>>>(g, ct_h, T_h, H, W, a);
-        k8_dt_cols<<<(W + 31) / 32, 32 * kColSegs, 0, s>>>(g, ct_v, T_v, H, W, a);
         const float* cur = g;
         for (int k = 1; k <= n_iter; ++k) {
-            const double rk = (double)sigma_s * std::sqrt(3.0) * std::pow(2.0, n_iter - k) /
-                              std::sqrt(std::pow(4.0, n_iter) - 1.0) * std::sqrt(3.0);
-            const float r = (float)rk;
-            const long long rq = (long long)std::floor((double)r * 8388608.0);
-            const int R = (int)std::floor(r);
             const bool last = k == n_iter;
-            nc_box_pass(cur, ct_h, T_h, va, ct_v, T_v, last ? e : vb, last ? g : nullptr, H, W,
-                        rq, R, num_sms, s);
+            nc_box_pass(cur, sh, va, sv, last ? e : vb, last ? g : nullptr, H, W, units(r[k - 1]),
+                        (int)std::floor(r[k - 1]), num_sms, s);
             cur = vb;
         }
     }
     return cudaGetLastError();
 }
 
-// two int64 transform planes and periods, four float planes
-size_t nc_scratch_floats(int H, int W) { return 8 * (size_t)H * W + 2 * ((size_t)H + (size_t)W); }
+// four float planes (the two fields, two pass buffers) and four planes of steps
+size_t nc_scratch_floats(int H, int W) { return 8 * (size_t)H * W; }
 
 }  // namespace blfls
