@@ -162,6 +162,22 @@ int blfls_smooth_rolling(blfls_handle *h, const float *img, float *out, int H, i
 int blfls_gaussian(blfls_handle *h, const float *img, float *out, int H, int W, int C,
                    float sigma, void *stream);
 
+/* ---- BLF-LS on normalised gradients (the paper's Section IV setting) -------------------- */
+
+/* BLF-LS (Eqs. 7-8) with every gradient field normalised to [0, 1] before the bilateral filter
+ * and restored after it, per channel and per field, in every pass (Section IV normalises images
+ * and gradients to [0, 1]).  The filter of Eq. 1 is exact under an affine map of its field (the
+ * weights sum to 1 and the range kernel sees only differences), so normalising a field of range
+ * R = max - min and restoring it is the filter with sigma_r R on the raw field: this is what the
+ * call computes, with R from the FP32 gradients (a constant field, R = 0, keeps sigma_r).  The
+ * result does not change when the image is scaled by any factor (scaled by it).  Arguments,
+ * precisions, radii and errors as blfls_smooth; device pointers [C][H][W], out may equal img.
+ * Each pass reads the fields' ranges back to the host, so the call synchronises `stream` once
+ * per pass, and the channels run one after another. */
+int blfls_smooth_normalized(blfls_handle *h, const float *img, float *out, int H, int W, int C,
+                            float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                            int prec, void *stream);
+
 /* ---- BLF-LS with the bilateral-grid filter (the fast approximation the paper uses) -------- */
 
 #define BLFLS_GRID_MAX_BYTES (8ull << 30)

@@ -7,6 +7,7 @@ Python binding) never does, and this package never imports the product path.
 from .blfls_ref import (  # noqa: F401
     blf,
     blf_at,
+    blf_field,
     blf_residuals,
     blfls,
     blfls_channel,

@@ -139,27 +139,43 @@ def solve_eq8(f: np.ndarray, vx: np.ndarray, vy: np.ndarray, lam: float) -> np.n
     return u.real
 
 
+def blf_field(g: np.ndarray, radius: int, sigma_s: float, sigma_r: float,
+              threads: int | None = None, normalize: bool = False) -> np.ndarray:
+    """Eq. 1 on one gradient field.  With `normalize` (Section IV normalises images and gradients
+    to [0, 1]) the field is mapped to [0, 1] by (g - min) / (max - min), filtered, and mapped
+    back; a constant field is returned unchanged."""
+    if not normalize:
+        return blf(g, radius, sigma_s, sigma_r, threads)
+    lo, hi = float(np.min(g)), float(np.max(g))
+    if hi == lo:
+        return np.array(g, dtype=np.float64)
+    return blf((g - lo) / (hi - lo), radius, sigma_s, sigma_r, threads) * (hi - lo) + lo
+
+
 def blfls_channel(f: np.ndarray, lam: float, sigma_s: float, sigma_r: float, radius: int,
-                  threads: int | None = None) -> np.ndarray:
-    """One BLF-LS pass on one channel: gradients -> BLF on each -> Eq. 8."""
+                  threads: int | None = None, normalize_grad: bool = False) -> np.ndarray:
+    """One BLF-LS pass on one channel: gradients -> BLF on each -> Eq. 8 (with
+    `normalize_grad`, each field normalised to [0, 1] around its filter)."""
     gx, gy = gradients(f)
-    vx = blf(gx, radius, sigma_s, sigma_r, threads)
-    vy = blf(gy, radius, sigma_s, sigma_r, threads)
+    vx = blf_field(gx, radius, sigma_s, sigma_r, threads, normalize_grad)
+    vy = blf_field(gy, radius, sigma_s, sigma_r, threads, normalize_grad)
     return solve_eq8(f, vx, vy, lam)
 
 
 def blfls(img: np.ndarray, lam: float, sigma_s: float, sigma_r: float, radius: int,
-          iters: int = 1, threads: int | None = None) -> np.ndarray:
+          iters: int = 1, threads: int | None = None, normalize_grad: bool = False) -> np.ndarray:
     """BLF-LS on a [C, H, W] (or [H, W]) image; returns FP64 of the same shape.
 
-    ``iters`` repeats the whole smoother, u_k = BLFLS(u_{k-1}); iters = 0 returns the input."""
+    ``iters`` repeats the whole smoother, u_k = BLFLS(u_{k-1}); iters = 0 returns the input.
+    ``normalize_grad`` normalises every gradient field of every pass to [0, 1] around its filter
+    (the setting of Section IV)."""
     a = np.asarray(img, dtype=np.float64)
     squeeze = a.ndim == 2
     if squeeze:
         a = a[None]
     u = a.copy()
     for _ in range(int(iters)):
-        u = np.stack([blfls_channel(u[c], lam, sigma_s, sigma_r, radius, threads)
+        u = np.stack([blfls_channel(u[c], lam, sigma_s, sigma_r, radius, threads, normalize_grad)
                       for c in range(u.shape[0])])
     return u[0] if squeeze else u
 

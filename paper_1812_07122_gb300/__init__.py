@@ -27,6 +27,7 @@ from .blfls import (  # noqa: F401
     blfls_smooth_host,
     blfls_smooth_ls,
     blfls_smooth_nc,
+    blfls_smooth_normalized,
     blfls_smooth_rolling,
     blfls_solve_residual,
     make_job,

@@ -117,6 +117,8 @@ _SIGNATURES = {
                                    _c_float, _c_int, _vp]),
     "blfls_smooth_nc": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _c_float,
                                  _c_float, _c_int, _c_int, _vp]),
+    "blfls_smooth_normalized": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float,
+                                         _c_float, _c_float, _c_int, _c_int, _c_int, _vp]),
 }
 
 
@@ -245,6 +247,15 @@ def blfls_smooth_grid(h, img, out, H, W, C, lam, sigma_s, sigma_r, iters=1, stre
     """BLF-LS with the bilateral-grid approximation of the BLF (synchronises once per pass)."""
     _check(load().blfls_smooth_grid(h, _ptr(img), _ptr(out), int(H), int(W), int(C), float(lam),
                                     float(sigma_s), float(sigma_r), int(iters), _stream(stream)), h)
+
+
+def blfls_smooth_normalized(h, img, out, H, W, C, lam, sigma_s, sigma_r, radius, iters=1,
+                            prec=BLFLS_FP32, stream=None) -> None:
+    """BLF-LS with every gradient field normalised to [0, 1] per channel (synchronises once per
+    pass)."""
+    _check(load().blfls_smooth_normalized(h, _ptr(img), _ptr(out), int(H), int(W), int(C),
+                                          float(lam), float(sigma_s), float(sigma_r), int(radius),
+                                          int(iters), _prec(prec), _stream(stream)), h)
 
 
 def blfls_smooth_nc(h, img, out, H, W, C, lam, sigma_s, sigma_r, iters=1, nc_iters=3,

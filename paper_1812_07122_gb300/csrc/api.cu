@@ -820,6 +820,75 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
     return BLFLS_OK;
 }
 
+// Pinned and device room for the per-pass range read-back of both fields of every channel.
+static int ensure_range_keys(blfls_handle* h)
+{
+    int rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "range keys");
+    if (rc != BLFLS_OK) return rc;
+    if (!h->grid_keys_host) {
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocHost(&p, sizeof(int) * 4 * BLFLS_MAX_CHANNELS);
+        if (e != cudaSuccess) return cuda_fail(e, "pinned range keys");
+        h->grid_keys_host = static_cast<int*>(p);
+    }
+    return BLFLS_OK;
+}
+
+int blfls_smooth_normalized(blfls_handle* h, const float* img, float* out, int H, int W, int C,
+                            float lambda, float sigma_s, float sigma_r, int radius, int iters,
+                            int prec, void* stream)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    int rc;
+    if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
+    if ((rc = check_blf_args(H, W, sigma_s, sigma_r, radius, prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(lambda)) != BLFLS_OK) return rc;
+    if (iters < 0 || iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters must lie in [0, BLFLS_MAX_ITERS]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)H * W;
+    if (iters == 0) {
+        if (out == img) return BLFLS_OK;
+        const cudaError_t e = cudaMemcpyAsync(out, img, plane * C * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BLFLS_OK : cuda_fail(e, "copy for iters = 0");
+    }
+    const FftPlanDev *rp = nullptr, *cp = nullptr;
+    if ((rc = prepare(h, H, W, radius, true, true, &rp, &cp)) != BLFLS_OK) return rc;
+    if ((rc = ensure_range_keys(h)) != BLFLS_OK) return rc;
+    const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
+    for (int it = 0; it < iters; ++it) {
+        const float* src = (it == 0) ? img : out;
+        // the ranges of both fields of every channel of this pass's input
+        cudaError_t e = launch_grid_minmax(src, H, W, C, h->grid_keys, s, h->num_sms);
+        if (e != cudaSuccess) return cuda_fail(e, "range kernel launch");
+        e = cudaMemcpyAsync(h->grid_keys_host, h->grid_keys, sizeof(int) * 4 * C,
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "range read-back");
+        for (int c = 0; c < C; ++c) {
+            BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
+            float scale[2];
+            for (int field = 0; field < 2; ++field) {
+                const int q = 2 * c + field;
+                const float lo = grid_key_to_float(h->grid_keys_host[2 * q]);
+                const float hi = grid_key_to_float(h->grid_keys_host[2 * q + 1]);
+                const float range = hi - lo;
+                scale[field] = range > 0.f ? range : 1.0f;   // a constant field is unchanged
+            }
+            bp.range_scale_x = scale[0];
+            bp.range_scale_y = scale[1];
+            const float* fc = src + c * plane;
+            e = blf_launch(h, fc, h->ex, h->ey, 1, bp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
+            e = solve_launch(h, fc, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+        }
+    }
+    return BLFLS_OK;
+}
+
 int blfls_smooth_nc(blfls_handle* h, const float* img, float* out, int H, int W, int C,
                     float lambda, float sigma_s, float sigma_r, int iters, int nc_iters,
                     void* stream)

@@ -46,8 +46,8 @@ template <bool RANGE>
 __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __restrict__ img,
                                                                float* __restrict__ ex,
                                                                float* __restrict__ ey, int H,
-                                                               int W, int R, int th, float kappa,
-                                                               float inv_kappa, float cs)
+                                                               int W, int R, int th, const Kap k,
+                                                               float cs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int fp = f_pitch(R), gp = g_pitch(R), gr = g_rows(R, th);
@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __re
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        gx[i] = grad_x(sf, fp, r, c, kappa);
-        gy[i] = grad_y(sf, fp, r, c, kappa);
+        gx[i] = grad_x(sf, fp, r, c, k.x);
+        gy[i] = grad_y(sf, fp, r, c, k.y);
     }
     __syncthreads();
     const int cx = threadIdx.x & (kTW - 1);
@@ -97,12 +97,12 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __re
         }
     }
     store_strip(ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W, x0 + cx, y0 + r0, ax, zx,
-                sx, ay, zy, sy, inv_kappa);
+                sx, ay, zy, sy, k);
 }
 
 // Radii above the tiled limit: gradients precomputed to global memory, one pixel per thread.
 __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ g, int H, int W,
-                             float kappa)
+                             float kx, float ky)
 {
     const size_t plane = (size_t)H * W;
     float* gx = g;
@@ -111,8 +111,8 @@ __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ 
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = int(i / W), x = int(i - (size_t)y * W);
         const float v = img[i];
-        gx[i] = kappa * (img[(size_t)y * W + (x + 1 == W ? 0 : x + 1)] - v);
-        gy[i] = kappa * (img[(size_t)(y + 1 == H ? 0 : y + 1) * W + x] - v);
+        gx[i] = kx * (img[(size_t)y * W + (x + 1 == W ? 0 : x + 1)] - v);
+        gy[i] = ky * (img[(size_t)(y + 1 == H ? 0 : y + 1) * W + x] - v);
     }
 }
 
@@ -121,7 +121,7 @@ __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ 
 template <bool RANGE>
 __global__ void k1_blf_global(const float* __restrict__ g, const float* __restrict__ hg,
                               float* __restrict__ ex, float* __restrict__ ey, int H, int W, int R,
-                              float inv_kappa, float cs)
+                              float inv_kx, float inv_ky, float cs)
 {
     const size_t plane = (size_t)H * W;
     const float* gx = g;
@@ -154,8 +154,8 @@ __global__ void k1_blf_global(const float* __restrict__ g, const float* __restri
                 zy += wy;
             }
         }
-        ex[i] = (__fdiv_rn(ax, zx) - sx) * inv_kappa;
-        ey[i] = (__fdiv_rn(ay, zy) - sy) * inv_kappa;
+        ex[i] = (__fdiv_rn(ax, zx) - sx) * inv_kx;
+        ey[i] = (__fdiv_rn(ay, zy) - sy) * inv_ky;
     }
 }
 
@@ -214,8 +214,10 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
 {
     const bool range = std::isfinite(p.sigma_r);
     const bool joint = p.guide != nullptr && range;   // without a range kernel the guide is moot
-    float kappa, inv_kappa, cs;
-    blf_constants(p.sigma_s, p.sigma_r, &kappa, &inv_kappa, &cs);
+    float kx, ikx, ky, iky, cs;
+    blf_constants(p.sigma_s, p.sigma_r * p.range_scale_x, &kx, &ikx, &cs);
+    blf_constants(p.sigma_s, p.sigma_r * p.range_scale_y, &ky, &iky, &cs);
+    const Kap k{kx, ky, ikx, iky};
     const int R = p.radius;
     const size_t plane = (size_t)p.H * p.W;
     if (joint ? R <= kMaxTemplR : R <= kMaxTiledR) {
@@ -225,18 +227,18 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
         if (joint) {
             JointFn fn = pick_joint_prec(p.prec, R);
             fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th, true), s>>>(
-                img, p.guide, p.guide_stride, ex, ey, p.H, p.W, th, kappa, inv_kappa, cs);
+                img, p.guide, p.guide_stride, ex, ey, p.H, p.W, th, k, cs);
         } else if (R <= kMaxTemplR) {
             TiledFn fn = pick_tiled_prec(p.prec, R, range);
             fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th), s>>>(img, ex, ey, p.H, p.W, th,
-                                                                         kappa, inv_kappa, cs);
+                                                                         k, cs);
         } else {
             if (p.prec != 0) return cudaErrorNotSupported;
             const size_t smem = tile_smem_bytes(R, sizeof(float), th);
             if (range)
-                k1_blf_tiled_rt<true><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, kappa, inv_kappa, cs);
+                k1_blf_tiled_rt<true><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs);
             else
-                k1_blf_tiled_rt<false><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, kappa, inv_kappa, cs);
+                k1_blf_tiled_rt<false><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs);
         }
         return cudaGetLastError();
     }
@@ -246,12 +248,12 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
     const int blocks = (int)std::min<size_t>((plane + 255) / 256, 4096);
     float* hg = joint ? gscratch + 2 * plane : nullptr;
     for (int c = 0; c < C; ++c) {
-        k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kappa);
-        if (joint) k1_gradients<<<blocks, 256, 0, s>>>(p.guide + c * p.guide_stride, hg, p.H, p.W, kappa);
+        k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kx, ky);
+        if (joint) k1_gradients<<<blocks, 256, 0, s>>>(p.guide + c * p.guide_stride, hg, p.H, p.W, kx, ky);
         if (range)
-            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, hg, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, hg, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs);
         else
-            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, nullptr, ex + c * plane, ey + c * plane, p.H, p.W, R, inv_kappa, cs);
+            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, nullptr, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs);
     }
     return cudaGetLastError();
 }

@@ -44,6 +44,13 @@ constexpr float kBig = 1e30f;    // exponent offset that turns a weight into exa
 
 using u64 = unsigned long long;
 
+// Range scaling of the two gradient fields: x' = kx g_x, y' = ky g_y (kappa of Eq. 1's range
+// kernel, see blf_constants; the fields differ only when each is normalised to its own range),
+// and the inverses that map residuals back.
+struct Kap {
+    float x, y, ix, iy;
+};
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -134,19 +141,19 @@ __device__ __forceinline__ float grad_y(const float* sf, int fp, int r, int c, f
     return kappa * (sf[(r + 1) * fp + c] - sf[r * fp + c]);
 }
 
-// e = (acc / Z - s') / kappa for the strip (FP32 accumulators), guarded against the image edge.
+// e = (acc / Z - s') / kappa (per field) for the strip (FP32 accumulators), guarded against the image edge.
 __device__ __forceinline__ void store_strip(float* __restrict__ ex, float* __restrict__ ey, int H,
                                             int W, int x, int ybase, const float* ax,
                                             const float* zx, const float* sx, const float* ay,
-                                            const float* zy, const float* sy, float inv_kappa)
+                                            const float* zy, const float* sy, const Kap k)
 {
     if (x >= W) return;
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
         const int y = ybase + j;
         if (y < H) {
-            ex[(size_t)y * W + x] = (__fdiv_rn(ax[j], zx[j]) - sx[j]) * inv_kappa;
-            ey[(size_t)y * W + x] = (__fdiv_rn(ay[j], zy[j]) - sy[j]) * inv_kappa;
+            ex[(size_t)y * W + x] = (__fdiv_rn(ax[j], zx[j]) - sx[j]) * k.ix;
+            ey[(size_t)y * W + x] = (__fdiv_rn(ay[j], zy[j]) - sy[j]) * k.iy;
         }
     }
 }
@@ -169,7 +176,7 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
                                                  const float* __restrict__ guide,
                                                  float* __restrict__ ex, float* __restrict__ ey,
                                                  int H, int W, int x0, int y0, int th,
-                                                 float kappa, float inv_kappa, float cs,
+                                                 const Kap k, float cs,
                                                  unsigned char* smem)
 {
     constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
@@ -181,7 +188,7 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        g[i] = make_float2(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+        g[i] = make_float2(grad_x(sf, fp, r, c, k.x), grad_y(sf, fp, r, c, k.y));
     }
     if constexpr (JOINT) {   // the guidance image's gradients, through the same f buffer
         __syncthreads();
@@ -189,7 +196,7 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
         __syncthreads();
         for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
             const int r = i / gp, c = i - r * gp;
-            hg[i] = make_float2(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+            hg[i] = make_float2(grad_x(sf, fp, r, c, k.x), grad_y(sf, fp, r, c, k.y));
         }
     }
     __syncthreads();
@@ -250,27 +257,27 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
         upk(Z[j], zx[j], zy[j]);
         upk(JOINT ? own_g[j * gp] : S[j], sx[j], sy[j]);   // the input's own gradient
     }
-    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sx, ay, zy, sy, inv_kappa);
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sx, ay, zy, sy, k);
 }
 
 template <int R, bool RANGE, bool JOINT>
 __device__ __forceinline__ void tile_f32(const float* __restrict__ f, const float* __restrict__ guide,
                                          float* __restrict__ ex,
                                          float* __restrict__ ey, int H, int W, int x0, int y0,
-                                         int th, float kappa, float inv_kappa, float cs,
+                                         int th, const Kap k, float cs,
                                          unsigned char* smem)
 {
-    tile_pair_fields<R, RANGE, false, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    tile_pair_fields<R, RANGE, false, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
 }
 
 template <int R, bool RANGE, bool JOINT>
 __device__ __forceinline__ void tile_bf16(const float* __restrict__ f, const float* __restrict__ guide,
                                           float* __restrict__ ex,
                                           float* __restrict__ ey, int H, int W, int x0, int y0,
-                                          int th, float kappa, float inv_kappa, float cs,
+                                          int th, const Kap k, float cs,
                                           unsigned char* smem)
 {
-    tile_pair_fields<R, RANGE, true, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    tile_pair_fields<R, RANGE, true, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -283,7 +290,7 @@ template <int R, bool RANGE, bool JOINT>
 __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const float* __restrict__ guide,
                                          float* __restrict__ ex,
                                          float* __restrict__ ey, int H, int W, int x0,
-                                         int y0, int th, float kappa, float inv_kappa,
+                                         int y0, int th, const Kap k,
                                          float cs, unsigned char* smem)
 {
     constexpr int fp = kTW + 2 * R + 1, gp = kTW + 2 * R;
@@ -295,7 +302,7 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const floa
     __syncthreads();
     for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
         const int r = i / gp, c = i - r * gp;
-        g[i] = __floats2half2_rn(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+        g[i] = __floats2half2_rn(grad_x(sf, fp, r, c, k.x), grad_y(sf, fp, r, c, k.y));
     }
 
     const int cx = threadIdx.x & (kTW - 1);
@@ -305,8 +312,8 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const floa
     float sxs[kStrip], sys[kStrip];
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
-        sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, kappa);   // FP32 centre values of the input
-        sys[j] = grad_y(sf, fp, R + r0 + j, R + cx, kappa);
+        sxs[j] = grad_x(sf, fp, R + r0 + j, R + cx, k.x);   // FP32 centre values of the input
+        sys[j] = grad_y(sf, fp, R + r0 + j, R + cx, k.y);
         A[j] = Z[j] = 0ull;
     }
     if constexpr (JOINT) {   // the guidance image's gradients, through the same f buffer
@@ -315,7 +322,7 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const floa
         __syncthreads();
         for (int i = threadIdx.x; i < gr * gp; i += blockDim.x) {
             const int r = i / gp, c = i - r * gp;
-            hg[i] = __floats2half2_rn(grad_x(sf, fp, r, c, kappa), grad_y(sf, fp, r, c, kappa));
+            hg[i] = __floats2half2_rn(grad_x(sf, fp, r, c, k.x), grad_y(sf, fp, r, c, k.y));
         }
     }
     __syncthreads();
@@ -371,19 +378,19 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const floa
         upk(A[j], ax[j], ay[j]);
         upk(Z[j], zx[j], zy[j]);
     }
-    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sxs, ay, zy, sys, inv_kappa);
+    store_strip(ex, ey, H, W, x0 + cx, y0 + r0, ax, zx, sxs, ay, zy, sys, k);
 }
 
 // JOINT: the range weights compare the gradients of `guide` (the joint filter of Section III-D);
 // the values averaged are still the gradients of f.
 template <int R, bool RANGE, int PREC, bool JOINT = false>
 __device__ __forceinline__ void blf_tile(const float* f, const float* guide, float* ex, float* ey,
-                                         int H, int W, int x0, int y0, int th, float kappa,
-                                         float inv_kappa, float cs, unsigned char* smem)
+                                         int H, int W, int x0, int y0, int th, const Kap k,
+                                         float cs, unsigned char* smem)
 {
-    if constexpr (PREC == 1) tile_f16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
-    else if constexpr (PREC == 2) tile_bf16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
-    else tile_f32<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, kappa, inv_kappa, cs, smem);
+    if constexpr (PREC == 1) tile_f16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
+    else if constexpr (PREC == 2) tile_bf16<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
+    else tile_f32<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
 }
 
 // One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.
@@ -391,14 +398,13 @@ template <int R, bool RANGE, int PREC>
 __global__ void __launch_bounds__(kMaxThreads) k1_blf(const float* __restrict__ img,
                                                       float* __restrict__ ex,
                                                       float* __restrict__ ey, int H, int W,
-                                                      int th, float kappa, float inv_kappa,
-                                                      float cs)
+                                                      int th, const Kap k, float cs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t plane = (size_t)H * W;
     blf_tile<R, RANGE, PREC>(img + blockIdx.z * plane, nullptr, ex + blockIdx.z * plane,
                              ey + blockIdx.z * plane, H, W, blockIdx.x * kTW, blockIdx.y * th,
-                             th, kappa, inv_kappa, cs, smem);
+                             th, k, cs, smem);
 }
 
 // Joint form: as k1_blf with the range kernel on, guided by channel z of `guide` (channel
@@ -409,15 +415,13 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_joint(const float* __restr
                                                             size_t gstride,
                                                             float* __restrict__ ex,
                                                             float* __restrict__ ey, int H, int W,
-                                                            int th, float kappa, float inv_kappa,
-                                                            float cs)
+                                                            int th, const Kap k, float cs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t plane = (size_t)H * W;
     blf_tile<R, true, PREC, true>(img + blockIdx.z * plane, guide + blockIdx.z * gstride,
                                   ex + blockIdx.z * plane, ey + blockIdx.z * plane, H, W,
-                                  blockIdx.x * kTW, blockIdx.y * th, th, kappa, inv_kappa, cs,
-                                  smem);
+                                  blockIdx.x * kTW, blockIdx.y * th, th, k, cs, smem);
 }
 
 // Batched form: a persistent grid walks every tile of every channel of the jobs of one
@@ -439,17 +443,17 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_batch(const BatchJob* __re
         const size_t plane = (size_t)J.H * J.W;
         __syncthreads();   // the previous tile's readers are done with shared memory
         blf_tile<R, RANGE, PREC>(J.src + c * plane, nullptr, J.ex + c * plane, J.ey + c * plane,
-                                 J.H, J.W, tx * kTW, ty * J.tile_h, J.tile_h, J.kappa,
-                                 J.inv_kappa, J.cs, smem);
+                                 J.H, J.W, tx * kTW, ty * J.tile_h, J.tile_h,
+                                 Kap{J.kappa, J.kappa, J.inv_kappa, J.inv_kappa}, J.cs, smem);
     }
 }
 
 }  // namespace
 
-using TiledFn = void (*)(const float*, float*, float*, int, int, int, float, float, float);
+using TiledFn = void (*)(const float*, float*, float*, int, int, int, const Kap, float);
 using BatchFn = void (*)(const BatchJob*, const int2*, int, int);
-using JointFn = void (*)(const float*, const float*, size_t, float*, float*, int, int, int, float,
-                         float, float);
+using JointFn = void (*)(const float*, const float*, size_t, float*, float*, int, int, int,
+                         const Kap, float);
 
 // Kernel pointers of one precision (defined in blf_f32.cu, blf_f16.cu, blf_bf16.cu).
 TiledFn pick_tiled_prec(int prec, int r, bool range);

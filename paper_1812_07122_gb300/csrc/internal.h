@@ -102,6 +102,9 @@ struct BlfParams {
     // guidance channel).
     const float* guide = nullptr;
     size_t guide_stride = 0;
+    // Range widths per field: field x uses sigma_r * range_scale_x, field y sigma_r *
+    // range_scale_y (1 and 1 unless each field is normalised to its own range).
+    float range_scale_x = 1.0f, range_scale_y = 1.0f;
 };
 
 // Launch K1 over channels [0, C) of img (planes of H*W floats).  `gscratch` must hold

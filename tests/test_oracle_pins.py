@@ -277,3 +277,38 @@ def test_residual_form_matches_eq8():
     du = np.linalg.solve(A, lam * (Dx.T @ ex[0].ravel() + Dy.T @ ey[0].ravel()))
     want = f + du.reshape(H, W)
     np.testing.assert_allclose(oracle.blfls(f, lam, 1.2, 0.15, 2), want, atol=1e-12)
+
+
+def test_normalised_gradients_are_the_filter_with_the_range_scaled():
+    """Section IV normalises the gradients to [0, 1]: normalising a field of range R around
+    Eq. 1 and restoring it equals Eq. 1 on the raw field with sigma_r R (the weights sum to 1 and
+    the range kernel sees only differences), per field and channel."""
+    f = np.random.default_rng(21).uniform(size=(2, 20, 24))
+    got = oracle.blfls(f, 20.0, 3.0, 0.1, 4, normalize_grad=True)
+    for c in range(2):
+        gx, gy = oracle.gradients(f[c])
+        rx, ry = gx.max() - gx.min(), gy.max() - gy.min()
+        want = oracle.solve_eq8(f[c], oracle.blf(gx, 4, 3.0, 0.1 * rx), oracle.blf(gy, 4, 3.0, 0.1 * ry),
+                                20.0)
+        np.testing.assert_allclose(got[c], want, rtol=0, atol=1e-12)
+
+
+def test_normalised_gradients_make_the_smoother_scale_invariant():
+    """With normalised gradients the result scales with the image (u(a f) = a u(f)); without
+    them it does not (sigma_r is absolute)."""
+    f = np.random.default_rng(22).uniform(size=(18, 22))
+    u1 = oracle.blfls(f, 30.0, 3.0, 0.1, 3, iters=2, normalize_grad=True)
+    u2 = oracle.blfls(3.7 * f, 30.0, 3.0, 0.1, 3, iters=2, normalize_grad=True)
+    np.testing.assert_allclose(u2, 3.7 * u1, rtol=0, atol=1e-12)
+    v1 = oracle.blfls(f, 30.0, 3.0, 0.1, 3)
+    v2 = oracle.blfls(3.7 * f, 30.0, 3.0, 0.1, 3)
+    assert np.max(np.abs(v2 - 3.7 * v1)) > 1e-3
+
+
+def test_normalised_constant_field_is_left_alone():
+    """A field of zero range (here the x-gradient of an image constant along x) is returned
+    unchanged, so its residual is zero."""
+    f = np.tile(np.random.default_rng(23).uniform(size=(16, 1)), (1, 12))
+    gx, _ = oracle.gradients(f)
+    assert np.all(gx == 0.0)
+    np.testing.assert_array_equal(oracle.blf_field(gx, 3, 2.0, 0.1, normalize=True), gx)
