@@ -8,6 +8,7 @@
 //   inverse FFTs, u = f + correction).
 #include "blfls.h"
 #include "handle.h"
+#include "nvtx_range.h"
 
 #include <cmath>
 #include <cstdio>
@@ -234,6 +235,7 @@ static int run_channel(blfls_handle* h, const float* img, float* out, const BlfP
     }
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
+        const NvtxRange range("pass");
         cudaError_t e = blf_launch(h, src, ex, ey, 1, bp, s);
         if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");
         e = solve_launch(h, src, ex, ey, out, rp, cp, sp, s, spec);
@@ -490,6 +492,7 @@ int blfls_smooth(blfls_handle* h, const float* img, float* out, int H, int W, in
                  float lambda, float sigma_s, float sigma_r, int radius, int iters, int prec,
                  void* stream)
 {
+    const NvtxRange range("blfls_smooth");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -506,6 +509,7 @@ int blfls_smooth_host(blfls_handle* h, const float* img_host, float* out_host, i
                       int C, float lambda, float sigma_s, float sigma_r, int radius, int iters,
                       int prec, void* stream)
 {
+    const NvtxRange range("blfls_smooth_host");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img_host, out_host, H, W, C)) != BLFLS_OK) return rc;
@@ -533,6 +537,7 @@ int blfls_smooth_host(blfls_handle* h, const float* img_host, float* out_host, i
 int blfls_smooth_ls(blfls_handle* h, const float* img, float* out, int H, int W, int C,
                     float lambda, int iters, void* stream)
 {
+    const NvtxRange range("blfls_smooth_ls");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -566,6 +571,7 @@ int blfls_layers(blfls_handle* h, const float* img, float* out, int H, int W, in
                  float strength, float lambda, float sigma_s, float sigma_r, int radius,
                  int iters, int prec, void* stream)
 {
+    const NvtxRange range("blfls_layers");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -655,6 +661,7 @@ static int gaussian_planes(blfls_handle* h, const float* in, float* out, int H, 
 int blfls_gaussian(blfls_handle* h, const float* img, float* out, int H, int W, int C, float sigma,
                    void* stream)
 {
+    const NvtxRange range("blfls_gaussian");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -668,6 +675,7 @@ int blfls_smooth_guided(blfls_handle* h, const float* img, const float* guide, f
                         int W, int C, int Cg, float lambda, float sigma_s, float sigma_r,
                         int radius, int iters, int prec, void* stream)
 {
+    const NvtxRange range("blfls_smooth_guided");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -705,6 +713,7 @@ int blfls_smooth_rolling(blfls_handle* h, const float* img, float* out, int H, i
                          float lambda, float sigma_s, float sigma_r, int radius, int iters,
                          float sigma_g, int prec, void* stream)
 {
+    const NvtxRange range("blfls_smooth_rolling");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -755,6 +764,7 @@ static int ensure_grid(blfls_handle* h, size_t cells)
 int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int W, int C,
                       float lambda, float sigma_s, float sigma_r, int iters, void* stream)
 {
+    const NvtxRange range("blfls_smooth_grid");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -838,6 +848,7 @@ int blfls_smooth_normalized(blfls_handle* h, const float* img, float* out, int H
                             float lambda, float sigma_s, float sigma_r, int radius, int iters,
                             int prec, void* stream)
 {
+    const NvtxRange range("blfls_smooth_normalized");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -893,6 +904,7 @@ int blfls_smooth_nc(blfls_handle* h, const float* img, float* out, int H, int W,
                     float lambda, float sigma_s, float sigma_r, int iters, int nc_iters,
                     void* stream)
 {
+    const NvtxRange range("blfls_smooth_nc");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -932,6 +944,7 @@ int blfls_smooth_nc(blfls_handle* h, const float* img, float* out, int H, int W,
 int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, int H, int W,
                        int C, float sigma_s, float sigma_r, int radius, int prec, void* stream)
 {
+    const NvtxRange range("blfls_blf_residual");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, ex, H, W, C)) != BLFLS_OK) return rc;
@@ -950,6 +963,7 @@ int blfls_blf_residual(blfls_handle* h, const float* img, float* ex, float* ey, 
 int blfls_solve_residual(blfls_handle* h, const float* img, const float* ex, const float* ey,
                          float* out, int H, int W, int C, float lambda, void* stream)
 {
+    const NvtxRange range("blfls_solve_residual");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     int rc;
     if ((rc = check_image_args(img, out, H, W, C)) != BLFLS_OK) return rc;
@@ -974,6 +988,7 @@ int blfls_solve_residual(blfls_handle* h, const float* img, const float* ex, con
 
 int blfls_smooth_batch(blfls_handle* h, const blfls_job* jobs, int n, void* stream)
 {
+    const NvtxRange range("blfls_smooth_batch");
     if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
     if (n < 0 || (n > 0 && !jobs)) return fail(BLFLS_EINVAL, "bad job list");
     for (int i = 0; i < n; ++i) {

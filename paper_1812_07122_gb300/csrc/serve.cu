@@ -18,6 +18,7 @@
 // host memory.  Nothing here waits without a bound: the scheduler sleeps on a condition variable
 // with a timeout, and blfls_server_wait takes a timeout.
 #include "handle.h"
+#include "nvtx_range.h"
 
 #include <algorithm>
 #include <atomic>
@@ -251,6 +252,7 @@ std::vector<Request*> select_batch(blfls_server* S)
 // lock NOT held: only this thread touches slots and the arena's device memory).
 void launch_batch(blfls_server* S, Slot* slot, const std::vector<Request*>& batch)
 {
+    const NvtxRange range("server batch");
     const double t = now_s();
     std::vector<blfls_job> jobs;
     jobs.reserve(batch.size());
