@@ -273,6 +273,15 @@ static bool ensure_channel_slots(blfls_handle* h, int C, size_t plane, size_t sp
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
         h->chan_streams.push_back(st);
     }
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    while ((int)h->chan_streams_graded.size() < C) {
+        const int c = (int)h->chan_streams_graded.size();
+        const int prio = std::min(least, greatest + c);   // lower number = higher priority
+        cudaStream_t st;
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess) return false;
+        h->chan_streams_graded.push_back(st);
+    }
     while ((int)h->chan_done.size() < C) {
         cudaEvent_t ev;
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
@@ -291,11 +300,12 @@ static int run_channels_concurrent(blfls_handle* h, const float* img, float* out
                                    size_t plane, size_t spec_elems, const BlfParams& bp,
                                    const SolveParams& sp, const FftPlanDev& rp,
                                    const FftPlanDev& cp, int iters, cudaStream_t s,
-                                   const cudaEvent_t* in_ready, const cudaEvent_t* done)
+                                   const cudaEvent_t* in_ready, const cudaEvent_t* done,
+                                   const std::vector<cudaStream_t>& streams)
 {
     cudaEventRecord(h->chan_fork, s);
     for (int c = 0; c < C; ++c) {
-        cudaStream_t sc = h->chan_streams[c];
+        cudaStream_t sc = streams[c];
         cudaStreamWaitEvent(sc, h->chan_fork, 0);
         if (in_ready) cudaStreamWaitEvent(sc, in_ready[c], 0);
         float *ex = nullptr, *ey = nullptr;
@@ -341,7 +351,7 @@ int blfls::run_smooth(blfls_handle* h, const float* img, float* out, int H, int 
     if (C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
         ensure_channel_slots(h, C, plane, spec_elems))
         return run_channels_concurrent(h, img, out, C, plane, spec_elems, bp, sp, *rp, *cp, iters,
-                                       s, nullptr, nullptr);
+                                       s, nullptr, nullptr, h->chan_streams);
     for (int c = 0; c < C; ++c)
         if ((rc = run_channel(h, img + c * plane, out + c * plane, bp, sp, *rp, *cp, iters, s)) != BLFLS_OK)
             return rc;
@@ -396,14 +406,20 @@ static int smooth_host_pipelined(blfls_handle* h, const float* img_host, float* 
     const bool par = C > 1 && !h->prof_on && radius <= blf_tiled_max_radius() &&
                      ensure_channel_slots(h, C, plane, spec_elems);
     if (par) {
+        // Graded priorities make the channels finish one after another, and each channel's
+        // result goes back on the channel's own stream as soon as it is done, so all but the
+        // last copy run under the remaining channels' compute.
         if ((rc = run_channels_concurrent(h, dimg, dout, C, plane, spec_elems, bp, sp, *rp, *cp,
-                                          iters, s, ev_in, ev_done)) != BLFLS_OK)
+                                          iters, s, ev_in, ev_done, h->chan_streams_graded)) != BLFLS_OK)
             return rc;
         for (int c = 0; c < C; ++c) {
-            if ((e = cudaStreamWaitEvent(cs, ev_done[c], 0)) != cudaSuccess) return cuda_fail(e, "stream wait");
+            cudaStream_t sc = h->chan_streams_graded[c];
             e = cudaMemcpyAsync(out_host + c * plane, dout + c * plane, plane * sizeof(float),
-                                cudaMemcpyDeviceToHost, cs);
+                                cudaMemcpyDeviceToHost, sc);
             if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+            if ((e = cudaEventRecord(h->chan_done[c], sc)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, h->chan_done[c], 0)) != cudaSuccess)
+                return cuda_fail(e, "stream ordering");
         }
     } else {
         for (int c = 0; c < C; ++c) {
@@ -477,6 +493,7 @@ void blfls_destroy(blfls_handle* h)
     if (h->nc_scratch) cudaFree(h->nc_scratch);
     if (h->chan_scratch) cudaFree(h->chan_scratch);
     for (cudaStream_t st : h->chan_streams) cudaStreamDestroy(st);
+    for (cudaStream_t st : h->chan_streams_graded) cudaStreamDestroy(st);
     for (cudaEvent_t ev : h->chan_done) cudaEventDestroy(ev);
     if (h->chan_fork) cudaEventDestroy(h->chan_fork);
     delete h;

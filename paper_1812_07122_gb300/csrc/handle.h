@@ -49,6 +49,9 @@ struct blfls_handle {
     float* chan_scratch = nullptr;
     size_t chan_cap = 0;             // floats
     std::vector<cudaStream_t> chan_streams;   // one per channel
+    // one per channel with graded priorities (channel 0 highest): the host-buffer path, where
+    // channels that finish one after another let each result's copy run under the others' work
+    std::vector<cudaStream_t> chan_streams_graded;
     std::vector<cudaEvent_t> chan_done;       // one per channel
     cudaEvent_t chan_fork = nullptr;
     // blfls_smooth_host: copy stream (non-blocking) and per-channel events
