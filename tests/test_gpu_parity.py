@@ -138,6 +138,27 @@ def test_smooth_matches_oracle(h, H, W, C, lam, ss, sr, r, iters):
         assert np.array_equal(got, f)
 
 
+@pytest.mark.parametrize("H,W", [(8192, 5), (5, 8192)])
+def test_maximum_dimension_lines(h, H, W):
+    """BLFLS_MAX_DIM along each axis (the plain FFT drivers take over where the staged buffers
+    no longer fit)."""
+    f = _img(H, W, 1, seed=H + W)
+    got = smooth(h, f, 20.0, 1.5, 0.1, 2, 1)
+    want = oracle.blfls(f, 20.0, 1.5, 0.1, 2, 1)
+    assert maxabs(got, want) <= TOL_FP32
+
+
+def test_maximum_dimension_square(h):
+    """8192 x 8192 (BLFLS_MAX_DIM on both axes), radius 2, one pass: every pixel against the
+    oracle (about half a minute of FP64 work on the host cores)."""
+    f = np.random.default_rng(5).uniform(size=(1, 8192, 8192)).astype(np.float32)
+    got = smooth(h, f, 30.0, 1.5, 0.1, 2, 1)
+    want = oracle.blfls(f, 30.0, 1.5, 0.1, 2, 1)
+    err = maxabs(got, want)
+    print(f"8192x8192 r=2: max-abs {err:.3e}")
+    assert err <= TOL_FP32, err
+
+
 def test_constant_image_and_radius_zero(h):
     f = np.full((1, 40, 56), 0.3125, dtype=np.float32)
     assert maxabs(smooth(h, f, 30.0, 3.0, 0.1, 5), f) <= 1e-6
