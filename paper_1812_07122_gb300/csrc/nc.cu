@@ -8,11 +8,9 @@
 // passes need only the steps, never ct itself.
 //
 //   k8_grad_steps  the two fields and, for each field, its steps along x and along y;
-//   k8_nc_rows_strip / k8_nc_cols_strip  one box pass of radius r along rows / columns for
-//                R = floor(r) <= 16: a thread takes a strip of 8 samples, holds the strip and R_max
-//                neighbours on either side (values and steps) in registers, forms the running
-//                sum of the steps over that window and scans each sample's run outward (rows are
-//                staged through shared memory);
+//   k8_nc_rows_tile / k8_nc_cols_tile  one box pass of radius r along rows / columns for
+//                R = floor(r) <= 64: tiles of values and steps (with R samples of neighbourhood)
+//                staged in shared memory, each pixel's run scanned outward there;
 //   k8_nc_rows / k8_nc_cols  larger radii: a sliding window per run of 32 samples;
 // N iterations with r_k = sigma_s sqrt(3) 2^(N-k) / sqrt(4^N - 1) sqrt(3), rows then columns; the
 // last column pass writes the residual e = v - g for the Fourier solve.
@@ -81,131 +79,144 @@ __global__ void __launch_bounds__(kNcThreads) k8_grad_steps(const float* __restr
 }
 
 // ---------------------------------------------------------------------------------------------
-// Box means for R = floor(r) <= RM.  The window holds samples q = 0..NW-1 of the unwrapped line
-// (positions p0 + q): values vw[q] and steps sw[q] (the step into sample q; sw[0] unused).
+// Box means for R = floor(r) <= kNcTileMaxR from shared-memory tiles.  A CTA stages a tile of the
+// values and the steps, with R samples of periodic neighbourhood on either side along the pass,
+// with coalesced loads; each thread then takes pixels whose lanes are adjacent along the tile's
+// fast axis (conflict-free reads) and scans each pixel's run outward in shared memory, adding
+// the steps until the distance exceeds the radius (at most R steps a side).
 // ---------------------------------------------------------------------------------------------
-constexpr int kNcStrip = 8;
+constexpr int kNcTileMaxR = 64;
+constexpr int kTileLong = 64;   // samples along the pass per tile
+constexpr int kTileWide = 32;   // lines per tile
+constexpr int kLoadBatch = 4;   // tile rows each warp loads with all their loads in flight
 
-template <int RM>
-__device__ __forceinline__ void strip_means(const unsigned (&sw)[kNcStrip + 2 * RM],
-                                            const float (&vw)[kNcStrip + 2 * RM], long long rq,
-                                            float (&mean)[kNcStrip])
+// One pixel's box mean: sample i of a staged line (s[p]: the step into p; v[p]: the value);
+// `st` is the distance between consecutive samples in shared memory.
+__device__ __forceinline__ float tile_mean(const unsigned* __restrict__ s,
+                                           const float* __restrict__ v, int st, int i, int R,
+                                           unsigned long long rq)
 {
-    constexpr int NW = kNcStrip + 2 * RM;
-    long long cw[NW];   // running sum of the steps over the window (window-relative transform)
-    cw[0] = 0;
-#pragma unroll
-    for (int q = 1; q < NW; ++q) cw[q] = cw[q - 1] + (long long)sw[q];
-#pragma unroll
-    for (int j = 0; j < kNcStrip; ++j) {
-        const long long top = cw[RM + j] + rq, bottom = cw[RM + j] - rq;
-        float acc = vw[RM + j], cnt = 1.f;
-        bool up = true, dn = true;
-#pragma unroll
-        for (int d = 1; d <= RM; ++d) {
-            up = up && cw[RM + j + d] <= top;
-            dn = dn && cw[RM + j - d] >= bottom;
-            if (up) { acc += vw[RM + j + d]; cnt += 1.f; }
-            if (dn) { acc += vw[RM + j - d]; cnt += 1.f; }
-        }
-        mean[j] = acc / cnt;
+    float acc = v[i * st], cnt = 1.f;
+    unsigned long long d = 0;
+    for (int k = 1; k <= R; ++k) {   // upwards
+        d += s[(i + k) * st];
+        if (d > rq) break;
+        acc += v[(i + k) * st];
+        cnt += 1.f;
     }
+    d = 0;
+    for (int k = 1; k <= R; ++k) {   // downwards: the step into i - k + 1
+        d += s[(i - k + 1) * st];
+        if (d > rq) break;
+        acc += v[(i - k) * st];
+        cnt += 1.f;
+    }
+    return acc / cnt;
 }
 
-// Along x: a CTA stages a tile of 32 rows x 64 columns of the values and the row steps, with RM
-// samples of periodic neighbourhood on either side, in shared memory with coalesced loads;
-// thread (lane, warp) takes row `lane` of the tile and a strip of kNcStrip columns (warp) and
-// reads the strip's window from shared memory (odd pitches put the lanes' rows in distinct
-// banks); the means go back through shared memory for coalesced stores.
-constexpr int kTileLong = kNcStrip * (kNcThreads / 32);   // 64 samples along the row
-constexpr int kTileWide = 32;                             // 32 rows
-
-template <int RM>
-__global__ void __launch_bounds__(kNcThreads) k8_nc_rows_strip(const float* __restrict__ v,
-                                                              const unsigned* __restrict__ sh,
-                                                              float* __restrict__ out, int H,
-                                                              int W, long long rq)
+// Along x: tiles of 32 rows x 64 columns; thread (lane, warp) takes columns lane and lane + 32
+// of rows warp, warp + 8, ... (coalesced stores).
+__global__ void __launch_bounds__(kNcThreads) k8_nc_rows_tile(const float* __restrict__ v,
+                                                             const unsigned* __restrict__ sh,
+                                                             float* __restrict__ out, int H,
+                                                             int W, int R, long long rq)
 {
-    constexpr int NW = kNcStrip + 2 * RM;
-    constexpr int SPAN = kTileLong + 2 * RM;
-    constexpr int PC = SPAN | 1, PO = kTileLong + 1;
-    __shared__ unsigned ss[kTileWide * PC];
-    __shared__ float sv[kTileWide * PC];
-    __shared__ float so[kTileWide * PO];
+    extern __shared__ __align__(16) unsigned char nc_smem[];
+    const int span = kTileLong + 2 * R;
+    unsigned* ss = reinterpret_cast<unsigned*>(nc_smem);
+    float* sv = reinterpret_cast<float*>(ss + kTileWide * span);
     const int tiles_x = (W + kTileLong - 1) / kTileLong;
     const int y0 = (blockIdx.x / tiles_x) * kTileWide, x0 = (blockIdx.x % tiles_x) * kTileLong;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int r = w; r < kTileWide; r += kNcThreads / 32) {
-        const int y = y0 + r;
-        if (y >= H) break;
-        for (int q = lane; q < SPAN; q += 32) {
-            int p = x0 - RM + q;                   // unwrapped column
+    // the tile's rows in groups of kLoadBatch per warp, all loads of a group in flight together
+    for (int r0 = w; r0 < kTileWide; r0 += kLoadBatch * (kNcThreads / 32)) {
+        for (int q = lane; q < span; q += 32) {
+            int p = x0 - R + q;                    // unwrapped column
             while (p < 0) p += W;
             while (p >= W) p -= W;
-            ss[r * PC + q] = sh[(size_t)y * W + p];
-            sv[r * PC + q] = v[(size_t)y * W + p];
-        }
-    }
-    __syncthreads();
-    if (y0 + lane < H) {
-        unsigned sw[NW];
-        float vw[NW];
+            unsigned a[kLoadBatch];
+            float b[kLoadBatch];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            sw[q] = ss[lane * PC + w * kNcStrip + q];
-            vw[q] = sv[lane * PC + w * kNcStrip + q];
-        }
-        float mean[kNcStrip];
-        strip_means<RM>(sw, vw, rq, mean);
+            for (int u = 0; u < kLoadBatch; ++u) {
+                const int y = y0 + r0 + u * (kNcThreads / 32);
+                if (r0 + u * (kNcThreads / 32) < kTileWide && y < H) {
+                    a[u] = sh[(size_t)y * W + p];
+                    b[u] = v[(size_t)y * W + p];
+                }
+            }
 #pragma unroll
-        for (int j = 0; j < kNcStrip; ++j) so[lane * PO + w * kNcStrip + j] = mean[j];
+            for (int u = 0; u < kLoadBatch; ++u) {
+                const int r = r0 + u * (kNcThreads / 32);
+                if (r < kTileWide && y0 + r < H) {
+                    ss[r * span + q] = a[u];
+                    sv[r * span + q] = b[u];
+                }
+            }
+        }
     }
     __syncthreads();
     for (int r = w; r < kTileWide; r += kNcThreads / 32) {
         const int y = y0 + r;
         if (y >= H) break;
-        for (int q = lane; q < kTileLong; q += 32)
-            if (x0 + q < W) out[(size_t)y * W + x0 + q] = so[r * PO + q];
+        for (int q = lane; q < kTileLong; q += 32) {
+            const int x = x0 + q;
+            if (x < W)
+                out[(size_t)y * W + x] = tile_mean(ss + r * span, sv + r * span, 1, R + q, R,
+                                                   (unsigned long long)rq);
+        }
     }
 }
 
-// Along y: one thread per strip of kNcStrip rows of one column, adjacent threads on adjacent
-// columns, the window loaded straight from global memory (coalesced across the warp; the
-// neighbouring strips' overlap comes from L1/L2); when g is not null the output is the
-// residual (mean - g).
-template <int RM>
-__global__ void __launch_bounds__(kNcThreads) k8_nc_cols_strip(const float* __restrict__ v,
-                                                              const unsigned* __restrict__ svs,
-                                                              float* __restrict__ out,
-                                                              const float* __restrict__ g,
-                                                              int H, int W, long long rq)
+// Along y: tiles of 64 rows x 32 columns; thread (lane, warp) takes column lane of rows warp,
+// warp + 8, ...; when g is not null the output is the residual (mean - g).
+__global__ void __launch_bounds__(kNcThreads) k8_nc_cols_tile(const float* __restrict__ v,
+                                                             const unsigned* __restrict__ svs,
+                                                             float* __restrict__ out,
+                                                             const float* __restrict__ g, int H,
+                                                             int W, int R, long long rq)
 {
-    constexpr int NW = kNcStrip + 2 * RM;
-    const int strips = (H + kNcStrip - 1) / kNcStrip;
-    const size_t total = (size_t)W * strips;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t / W), x = (int)(t - (size_t)k * W);
-        int m = k * kNcStrip - RM;
-        while (m < 0) m += H;
-        unsigned sw[NW];
-        float vw[NW];
+    extern __shared__ __align__(16) unsigned char nc_smem[];
+    const int span = kTileLong + 2 * R;
+    unsigned* ss = reinterpret_cast<unsigned*>(nc_smem);
+    float* sv = reinterpret_cast<float*>(ss + span * kTileWide);
+    const int tiles_x = (W + kTileWide - 1) / kTileWide;
+    const int y0 = (blockIdx.x / tiles_x) * kTileLong, x0 = (blockIdx.x % tiles_x) * kTileWide;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 + lane;
+    if (x < W) {
+        // rows of the tile in groups of kLoadBatch per warp, all loads of a group in flight
+        for (int q0 = w; q0 < span; q0 += kLoadBatch * (kNcThreads / 32)) {
+            unsigned a[kLoadBatch];
+            float b[kLoadBatch];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            sw[q] = svs[(size_t)m * W + x];
-            vw[q] = v[(size_t)m * W + x];
-            if (++m == H) m = 0;
-        }
-        float mean[kNcStrip];
-        strip_means<RM>(sw, vw, rq, mean);
+            for (int u = 0; u < kLoadBatch; ++u) {
+                const int q = q0 + u * (kNcThreads / 32);
+                if (q < span) {
+                    int p = y0 - R + q;            // unwrapped row
+                    while (p < 0) p += H;
+                    while (p >= H) p -= H;
+                    a[u] = svs[(size_t)p * W + x];
+                    b[u] = v[(size_t)p * W + x];
+                }
+            }
 #pragma unroll
-        for (int j = 0; j < kNcStrip; ++j) {
-            const int y = k * kNcStrip + j;
-            if (y < H) {
-                const size_t i = (size_t)y * W + x;
-                out[i] = g ? mean[j] - g[i] : mean[j];
+            for (int u = 0; u < kLoadBatch; ++u) {
+                const int q = q0 + u * (kNcThreads / 32);
+                if (q < span) {
+                    ss[q * kTileWide + lane] = a[u];
+                    sv[q * kTileWide + lane] = b[u];
+                }
             }
         }
+    }
+    __syncthreads();
+    if (x >= W) return;
+    for (int q = w; q < kTileLong; q += kNcThreads / 32) {
+        const int y = y0 + q;
+        if (y >= H) break;
+        const float m = tile_mean(ss + lane, sv + lane, kTileWide, R + q, R, (unsigned long long)rq);
+        const size_t i = (size_t)y * W + x;
+        out[i] = g ? m - g[i] : m;
     }
 }
 
@@ -327,28 +338,21 @@ int nc_blocks(size_t n, int num_sms)
     return (int)std::max<size_t>(1, std::min(want, (size_t)num_sms * 8));
 }
 
-template <int RM>
-void box_pass_strips(const float* v, const unsigned* sh, float* mid, const unsigned* sv,
-                     float* out, const float* g, int H, int W, long long rq, int num_sms,
-                     cudaStream_t s)
-{
-    const int row_tiles = ((H + kTileWide - 1) / kTileWide) * ((W + kTileLong - 1) / kTileLong);
-    k8_nc_rows_strip<RM><<<row_tiles, kNcThreads, 0, s>>>(v, sh, mid, H, W, rq);
-    const size_t strips = (size_t)W * ((H + kNcStrip - 1) / kNcStrip);
-    k8_nc_cols_strip<RM><<<nc_blocks(strips, num_sms), kNcThreads, 0, s>>>(mid, sv, out, g, H, W,
-                                                                          rq);
-}
+size_t nc_tile_smem(int R) { return (size_t)(kTileLong + 2 * R) * kTileWide * 8; }
 
 // One iteration: box means along the rows of v into mid, then along the columns of mid into out
-// (minus g when given).  Strip kernels for R <= 16, sliding windows above.
+// (minus g when given).  Shared-memory tiles for R <= kNcTileMaxR, sliding windows above.
 void nc_box_pass(const float* v, const unsigned* sh, float* mid, const unsigned* sv, float* out,
                  const float* g, int H, int W, long long rq, int R, int num_sms, cudaStream_t s)
 {
-    if (R <= 1) return box_pass_strips<1>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
-    if (R <= 2) return box_pass_strips<2>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
-    if (R <= 4) return box_pass_strips<4>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
-    if (R <= 8) return box_pass_strips<8>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
-    if (R <= 16) return box_pass_strips<16>(v, sh, mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= kNcTileMaxR) {
+        const size_t smem = nc_tile_smem(R);
+        const int row_tiles = ((H + kTileWide - 1) / kTileWide) * ((W + kTileLong - 1) / kTileLong);
+        k8_nc_rows_tile<<<row_tiles, kNcThreads, smem, s>>>(v, sh, mid, H, W, R, rq);
+        const int col_tiles = ((H + kTileLong - 1) / kTileLong) * ((W + kTileWide - 1) / kTileWide);
+        k8_nc_cols_tile<<<col_tiles, kNcThreads, smem, s>>>(mid, sv, out, g, H, W, R, rq);
+        return;
+    }
     k8_nc_rows<<<nc_blocks((size_t)H * ((W + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(
         v, sh, mid, H, W, rq);
     k8_nc_cols<<<nc_blocks((size_t)W * ((H + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(

@@ -48,9 +48,9 @@ def _nc(h, f, lam, ss, sr, iters=1, nc_iters=3, inplace=False):
     (100, 37, 1, 1024.0, 12.0, 0.05, 1, 3), # radius above a third of the width (wrapping boxes)
     (33, 45, 1, 20.0, 4.0, math.inf, 1, 2), # plain box iterations
     (211, 64, 1, 20.0, 2.0, 0.2, 1, 1),     # prime height (Bluestein solve), one iteration
-    (72, 96, 2, 30.0, 8.0, 0.1, 1, 3),      # box radii 12, 6, 3: every strip-kernel size
+    (72, 96, 2, 30.0, 8.0, 0.1, 1, 3),      # box radii 12, 6, 3
     (24, 7, 1, 20.0, 8.0, 0.1, 1, 3),       # radii above the width: boxes wrap several periods
-    (9, 130, 1, 20.0, 30.0, 0.5, 1, 2),     # radii 46 and 23: the sliding-window passes
+    (9, 130, 1, 20.0, 45.0, 0.5, 1, 2),     # radii 69 (sliding-window passes) and 34 (tiles)
 ])
 def test_ncls_matches_oracle(h, H, W, C, lam, ss, sr, iters, nit):
     f = _img(H, W, C, seed=7 * H + W)
