@@ -70,3 +70,24 @@ def test_job_struct_matches_the_header():
     # pointer, pointer, 3 ints, 3 floats, 3 ints
     ps = ctypes.sizeof(ctypes.c_void_p)
     assert ctypes.sizeof(blfls.blfls_job) == 2 * ps + 9 * 4 + (4 if ps == 8 else 0)
+
+
+@pytest.mark.parametrize("name,args", [
+    ("blfls_smooth_host", (1, 1, 8, 8, 1, 1.0, 1.0, 0.1, 1, 1, 0, None)),
+    ("blfls_smooth_ls", (1, 1, 8, 8, 1, 1.0, 1, None)),
+    ("blfls_layers", (1, 1, 8, 8, 1, 0, 2.0, 1.0, 1.0, 0.1, 1, 1, 0, None)),
+    ("blfls_gaussian", (1, 1, 8, 8, 1, 1.0, None)),
+    ("blfls_smooth_guided", (1, 1, 1, 8, 8, 1, 1, 1.0, 1.0, 0.1, 1, 1, 0, None)),
+    ("blfls_smooth_rolling", (1, 1, 8, 8, 1, 1.0, 1.0, 0.1, 1, 1, 1.0, 0, None)),
+    ("blfls_smooth_grid", (1, 1, 8, 8, 1, 1.0, 1.0, 0.1, 1, None)),
+    ("blfls_smooth_nc", (1, 1, 8, 8, 1, 1.0, 1.0, 0.1, 1, 3, None)),
+    ("blfls_smooth_normalized", (1, 1, 8, 8, 1, 1.0, 1.0, 0.1, 1, 1, 0, None)),
+    ("blfls_blf_residual", (1, 1, 1, 8, 8, 1, 1.0, 0.1, 1, 0, None)),
+    ("blfls_solve_residual", (1, 1, 1, 1, 8, 8, 1, 1.0, None)),
+    ("blfls_smooth_batch", (None, 0, None)),
+    ("blfls_profile_begin", (16,)),
+])
+def test_every_entry_point_rejects_a_null_handle_on_the_host(lib, name, args):
+    """Argument checks run on the host before anything touches the GPU: a NULL handle is
+    BLFLS_EINVAL from every entry point that takes one."""
+    assert getattr(lib, name)(None, *args) == blfls.BLFLS_EINVAL
