@@ -8,9 +8,11 @@
 // passes need only the steps, never ct itself.
 //
 //   k8_grad_steps  the two fields and, for each field, its steps along x and along y;
-//   k8_nc_rows_tile / k8_nc_cols_tile  one box pass of radius r along rows / columns for
-//                R = floor(r) <= 64: tiles of values and steps (with R samples of neighbourhood)
-//                staged in shared memory, each pixel's run scanned outward there;
+//   k8_nc_rows_tile  one box pass of radius r along rows for R = floor(r) <= 64: tiles of values
+//                and steps (with R samples of neighbourhood) staged in shared memory, each
+//                pixel's run scanned outward there;
+//   k8_nc_cols_strip  the pass along columns for R <= 16: a thread holds a strip of 8 samples and
+//                its neighbourhood in registers (coalesced loads straight from global memory);
 //   k8_nc_rows / k8_nc_cols  larger radii: a sliding window per run of 32 samples;
 // N iterations with r_k = sigma_s sqrt(3) 2^(N-k) / sqrt(4^N - 1) sqrt(3), rows then columns; the
 // last column pass writes the residual e = v - g for the Fourier solve.
@@ -167,56 +169,77 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_rows_tile(const float* __res
     }
 }
 
-// Along y: tiles of 64 rows x 32 columns; thread (lane, warp) takes column lane of rows warp,
-// warp + 8, ...; when g is not null the output is the residual (mean - g).
-__global__ void __launch_bounds__(kNcThreads) k8_nc_cols_tile(const float* __restrict__ v,
-                                                             const unsigned* __restrict__ svs,
-                                                             float* __restrict__ out,
-                                                             const float* __restrict__ g, int H,
-                                                             int W, int R, long long rq)
+// Along y the columns are loaded straight from global memory instead (adjacent threads on
+// adjacent columns, so every load is coalesced): a thread takes a strip of kNcStrip samples of
+// one column and holds the strip and RM neighbours on either side (values and steps) in
+// registers, with one load per sample; the running sum of the steps over that window gives the
+// window-relative transform, and each sample's run is scanned outward over the registers with
+// every comparison predicated (R = floor(r) <= RM).
+constexpr int kNcStrip = 8;
+
+template <int RM>
+__device__ __forceinline__ void strip_means(const unsigned (&sw)[kNcStrip + 2 * RM],
+                                            const float (&vw)[kNcStrip + 2 * RM], long long rq,
+                                            float (&mean)[kNcStrip])
 {
-    extern __shared__ __align__(16) unsigned char nc_smem[];
-    const int span = kTileLong + 2 * R;
-    unsigned* ss = reinterpret_cast<unsigned*>(nc_smem);
-    float* sv = reinterpret_cast<float*>(ss + span * kTileWide);
-    const int tiles_x = (W + kTileWide - 1) / kTileWide;
-    const int y0 = (blockIdx.x / tiles_x) * kTileLong, x0 = (blockIdx.x % tiles_x) * kTileWide;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = x0 + lane;
-    if (x < W) {
-        // rows of the tile in groups of kLoadBatch per warp, all loads of a group in flight
-        for (int q0 = w; q0 < span; q0 += kLoadBatch * (kNcThreads / 32)) {
-            unsigned a[kLoadBatch];
-            float b[kLoadBatch];
+    constexpr int NW = kNcStrip + 2 * RM;
+    long long cw[NW];   // running sum of the steps over the window (window-relative transform)
+    cw[0] = 0;
 #pragma unroll
-            for (int u = 0; u < kLoadBatch; ++u) {
-                const int q = q0 + u * (kNcThreads / 32);
-                if (q < span) {
-                    int p = y0 - R + q;            // unwrapped row
-                    while (p < 0) p += H;
-                    while (p >= H) p -= H;
-                    a[u] = svs[(size_t)p * W + x];
-                    b[u] = v[(size_t)p * W + x];
-                }
-            }
+    for (int q = 1; q < NW; ++q) cw[q] = cw[q - 1] + (long long)sw[q];
 #pragma unroll
-            for (int u = 0; u < kLoadBatch; ++u) {
-                const int q = q0 + u * (kNcThreads / 32);
-                if (q < span) {
-                    ss[q * kTileWide + lane] = a[u];
-                    sv[q * kTileWide + lane] = b[u];
-                }
+    for (int j = 0; j < kNcStrip; ++j) {
+        const long long top = cw[RM + j] + rq, bottom = cw[RM + j] - rq;
+        float acc = vw[RM + j], cnt = 1.f;
+        bool up = true, dn = true;
+#pragma unroll
+        for (int d = 1; d <= RM; ++d) {
+            up = up && cw[RM + j + d] <= top;
+            dn = dn && cw[RM + j - d] >= bottom;
+            if (up) { acc += vw[RM + j + d]; cnt += 1.f; }
+            if (dn) { acc += vw[RM + j - d]; cnt += 1.f; }
+        }
+        mean[j] = acc / cnt;
+    }
+}
+
+// Along y: one thread per strip of kNcStrip rows of one column, adjacent threads on adjacent
+// columns, the window loaded straight from global memory (coalesced across the warp; the
+// neighbouring strips' overlap comes from L1/L2); when g is not null the output is the
+// residual (mean - g).
+template <int RM>
+__global__ void __launch_bounds__(kNcThreads) k8_nc_cols_strip(const float* __restrict__ v,
+                                                              const unsigned* __restrict__ svs,
+                                                              float* __restrict__ out,
+                                                              const float* __restrict__ g,
+                                                              int H, int W, long long rq)
+{
+    constexpr int NW = kNcStrip + 2 * RM;
+    const int strips = (H + kNcStrip - 1) / kNcStrip;
+    const size_t total = (size_t)W * strips;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / W), x = (int)(t - (size_t)k * W);
+        int m = k * kNcStrip - RM;
+        while (m < 0) m += H;
+        unsigned sw[NW];
+        float vw[NW];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            sw[q] = svs[(size_t)m * W + x];
+            vw[q] = v[(size_t)m * W + x];
+            if (++m == H) m = 0;
+        }
+        float mean[kNcStrip];
+        strip_means<RM>(sw, vw, rq, mean);
+#pragma unroll
+        for (int j = 0; j < kNcStrip; ++j) {
+            const int y = k * kNcStrip + j;
+            if (y < H) {
+                const size_t i = (size_t)y * W + x;
+                out[i] = g ? mean[j] - g[i] : mean[j];
             }
         }
-    }
-    __syncthreads();
-    if (x >= W) return;
-    for (int q = w; q < kTileLong; q += kNcThreads / 32) {
-        const int y = y0 + q;
-        if (y >= H) break;
-        const float m = tile_mean(ss + lane, sv + lane, kTileWide, R + q, R, (unsigned long long)rq);
-        const size_t i = (size_t)y * W + x;
-        out[i] = g ? m - g[i] : m;
     }
 }
 
@@ -340,21 +363,33 @@ int nc_blocks(size_t n, int num_sms)
 
 size_t nc_tile_smem(int R) { return (size_t)(kTileLong + 2 * R) * kTileWide * 8; }
 
+template <int RM>
+void cols_strips(const float* mid, const unsigned* sv, float* out, const float* g, int H, int W,
+                 long long rq, int num_sms, cudaStream_t s)
+{
+    const size_t strips = (size_t)W * ((H + kNcStrip - 1) / kNcStrip);
+    k8_nc_cols_strip<RM><<<nc_blocks(strips, num_sms), kNcThreads, 0, s>>>(mid, sv, out, g, H, W,
+                                                                          rq);
+}
+
 // One iteration: box means along the rows of v into mid, then along the columns of mid into out
-// (minus g when given).  Shared-memory tiles for R <= kNcTileMaxR, sliding windows above.
+// (minus g when given).  Rows: shared-memory tiles for R <= kNcTileMaxR; columns: register strips
+// for R <= 16; sliding windows above.
 void nc_box_pass(const float* v, const unsigned* sh, float* mid, const unsigned* sv, float* out,
                  const float* g, int H, int W, long long rq, int R, int num_sms, cudaStream_t s)
 {
     if (R <= kNcTileMaxR) {
-        const size_t smem = nc_tile_smem(R);
         const int row_tiles = ((H + kTileWide - 1) / kTileWide) * ((W + kTileLong - 1) / kTileLong);
-        k8_nc_rows_tile<<<row_tiles, kNcThreads, smem, s>>>(v, sh, mid, H, W, R, rq);
-        const int col_tiles = ((H + kTileLong - 1) / kTileLong) * ((W + kTileWide - 1) / kTileWide);
-        k8_nc_cols_tile<<<col_tiles, kNcThreads, smem, s>>>(mid, sv, out, g, H, W, R, rq);
-        return;
+        k8_nc_rows_tile<<<row_tiles, kNcThreads, nc_tile_smem(R), s>>>(v, sh, mid, H, W, R, rq);
+    } else {
+        k8_nc_rows<<<nc_blocks((size_t)H * ((W + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0,
+                     s>>>(v, sh, mid, H, W, rq);
     }
-    k8_nc_rows<<<nc_blocks((size_t)H * ((W + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(
-        v, sh, mid, H, W, rq);
+    if (R <= 1) return cols_strips<1>(mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 2) return cols_strips<2>(mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 4) return cols_strips<4>(mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 8) return cols_strips<8>(mid, sv, out, g, H, W, rq, num_sms, s);
+    if (R <= 16) return cols_strips<16>(mid, sv, out, g, H, W, rq, num_sms, s);
     k8_nc_cols<<<nc_blocks((size_t)W * ((H + kNcRun - 1) / kNcRun), num_sms), kNcThreads, 0, s>>>(
         mid, sv, out, g, H, W, rq);
 }
