@@ -315,6 +315,38 @@ def bench_serving(dev, n_req, rate):
             "warmup_requests": warm["completed"]}
 
 
+def hbm_peak_gbs():
+    """(peak GB/s, basis): the measured copy bandwidth of the GB300s when the driver has
+    written it, else the fallback figure."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(rec["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
+def solve_rooflines(prof_ms, prof_n, H, W):
+    """K2-K4 against the HBM roofline: algorithmic bytes per launch (one channel) over the
+    average launch time of the profiled loop.  K2 reads e_x, e_y and writes the half spectrum;
+    K3 reads and writes the half spectrum; K4 reads it and f and writes u."""
+    try:
+        spec = H * (W // 2 + 1) * 8
+        plane = H * W * 4
+        algo = {"K2": 2 * plane + spec, "K3": 2 * spec, "K4": spec + 2 * plane}
+        peak, basis = hbm_peak_gbs()
+        out = {"unit": "GB/s", "peak": peak, "peak_basis": basis}
+        for i, k in ((1, "K2"), (2, "K3"), (3, "K4")):
+            if prof_n[i] <= 0:
+                continue
+            ms = prof_ms[i] / prof_n[i]
+            gbs = algo[k] / (ms / 1e3) / 1e9
+            out[k] = {"ms_per_launch": round(ms, 4), "algorithmic_bytes": algo[k],
+                      "achieved": round(gbs, 1), "frac": round(gbs / peak, 4)}
+        return out
+    except (TypeError, ValueError, IndexError, ZeroDivisionError):
+        return None
+
+
 def k1_traffic_per_launch():
     """DRAM bytes per K1 launch from the committed ncu summary, if it was taken on the current
     kernel source (else None)."""
@@ -442,7 +474,8 @@ def main():
                           f"{ms_per_step_in_order:.3f}); `value` comes from the loop with "
                           "concurrent channel streams",
                 "stage_share": {k: round(v / total_prof, 4) for k, v in
-                                zip(["K1", "K2", "K3", "K4"], prof_ms)} if total_prof else None}
+                                zip(["K1", "K2", "K3", "K4"], prof_ms)} if total_prof else None,
+                "solve_kernels": solve_rooflines(prof_ms, prof_n, H, W)}
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
