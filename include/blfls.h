@@ -95,10 +95,13 @@ int blfls_smooth(blfls_handle *h, const float *img, float *out, int H, int W, in
                  void *stream);
 
 /* The same smoother on HOST buffers: copies img to the device, smooths, copies the result to
- * out and waits for the stream.  img/out are host pointers; with pinned memory the copies run
- * on the handle's own copy stream, one channel at a time, under the computation of the other
- * channels (the channels are smoothed one after another on `stream`).  out may equal img.  The
- * device copies live in the handle's scratch memory. */
+ * out and waits for the stream.  img/out are host pointers; with pinned memory the uploads run
+ * one channel at a time on the handle's own copy stream, each channel starts as soon as its
+ * data has landed, the channels run side by side on streams of graded priority (so they finish
+ * one after another), and each result is copied back on its channel's stream as soon as it is
+ * done, under the remaining channels' work (when the budget has no room for per-channel
+ * scratch, the channels run one after another on `stream`).  out may equal img.  The device
+ * copies live in the handle's scratch memory. */
 int blfls_smooth_host(blfls_handle *h, const float *img_host, float *out_host, int H, int W,
                       int C, float lambda, float sigma_s, float sigma_r, int radius, int iters,
                       int prec, void *stream);
