@@ -24,5 +24,13 @@ from .guided_ref import (  # noqa: F401
     gaussian,
     gaussian_weights,
 )
-from .grid_ref import blf_grid, blfls_grid, grid_shape  # noqa: F401
-from .nc_ref import domain_transform, nc_filter, nc_pass, nc_schedule, ncls  # noqa: F401
+from .grid_ref import blf_grid, blfls_grid, grid_shape, grid_z_coords  # noqa: F401
+from .nc_ref import (  # noqa: F401
+    domain_transform,
+    increments,
+    nc_filter,
+    nc_margins,
+    nc_pass,
+    nc_schedule,
+    ncls,
+)

@@ -22,10 +22,16 @@ notes), for one field g of size H x W with spatial and range parameters sigma_s,
 
 Image borders are open (the grid is not periodic), as in the grid method itself.
 
-The cell of a pixel is an integer decided by floating point, so it is decided in FP32 exactly as
-the CUDA kernel takes it: t = x / s_s (IEEE FP32 division) + 1/2, floor; z likewise from
-(g - min g) / s_r with g and min g in FP32.  Everything else (the sums, blur and interpolation)
-is FP64 on the values as given.
+Everything is FP64 on the values as given: the gradients are the exact FP64 differences of the
+input, min g their exact minimum, and the cell of a pixel is floor(t + 1/2) of the FP64 value of
+t.  sigma_s and sigma_r enter as the FP32 values the C interface receives.
+
+A cell is an integer decided by a real number, so an implementation that holds the gradients in
+a narrower type can land on the other side of a rounding boundary when t is within that type's
+rounding of it.  ``grid_z_coords`` exposes the FP64 range coordinate t of every pixel (so a test
+can find those pixels) and ``blf_grid`` / ``blfls_grid`` accept ``flip`` masks that put the
+marked pixels in the other candidate cell (the neighbour across the nearest boundary), so a test
+can evaluate the definition with either decision.
 """
 from __future__ import annotations
 
@@ -39,11 +45,33 @@ PAD = 2
 _EDGE = math.exp(-0.5)
 
 
+def _params(sigma_s: float, sigma_r: float) -> tuple[float, float]:
+    """sigma_s, sigma_r as the FP32 values the C interface receives, widened to FP64."""
+    return float(np.float32(sigma_s)), float(np.float32(sigma_r))
+
+
 def grid_shape(H: int, W: int, lo: float, hi: float, sigma_s: float, sigma_r: float):
     gx = int(math.floor((W - 1) / sigma_s)) + 1 + 2 * PAD
     gy = int(math.floor((H - 1) / sigma_s)) + 1 + 2 * PAD
     gz = int(math.floor((hi - lo) / sigma_r)) + 1 + 2 * PAD
     return gz, gy, gx
+
+
+def grid_z_coords(g: np.ndarray, sigma_r: float) -> tuple[np.ndarray, float]:
+    """The FP64 range coordinate t = (g - min g) / s_r + 1/2 whose floor is a pixel's range cell
+    (before the padding), and min g."""
+    g = np.asarray(g, dtype=np.float64)
+    _, sr = _params(1.0, sigma_r)
+    lo = float(g.min())
+    return (g - lo) / sr + 0.5, lo
+
+
+def _flipped_cell(t: np.ndarray) -> np.ndarray:
+    """The other candidate cell of a coordinate near a rounding boundary: the neighbour of
+    floor(t) across the nearest integer."""
+    n = np.floor(t)
+    near = np.rint(t)
+    return np.where(n == near, n - 1.0, n + 1.0)
 
 
 def _blur_axis(a: np.ndarray, axis: int) -> np.ndarray:
@@ -73,23 +101,27 @@ def _trilinear(grid: np.ndarray, z: np.ndarray, y: np.ndarray, x: np.ndarray) ->
     return out
 
 
-def blf_grid(g: np.ndarray, sigma_s: float, sigma_r: float) -> np.ndarray:
-    """The bilateral-grid approximation of Eq. 1 on one field (FP64)."""
+def blf_grid(g: np.ndarray, sigma_s: float, sigma_r: float,
+             flip: np.ndarray | None = None) -> np.ndarray:
+    """The bilateral-grid approximation of Eq. 1 on one field (FP64).  `flip` (bool, H x W)
+    puts the marked pixels in their other candidate range cell (see the module notes)."""
     g = np.asarray(g, dtype=np.float64)
     H, W = g.shape
-    g32 = g.astype(np.float32)
-    lo32, hi32 = g32.min(), g32.max()
-    ss32, sr32, half = np.float32(sigma_s), np.float32(sigma_r), np.float32(0.5)
-    gz, gy, gx = grid_shape(H, W, float(lo32), float(hi32), float(ss32), float(sr32))
-    yy, xx = np.mgrid[0:H, 0:W]
-    # cells: FP32 decisions (see the module notes)
-    cz = np.floor((g32 - lo32) / sr32 + half).astype(int) + PAD
-    cy = np.floor(yy.astype(np.float32) / ss32 + half).astype(int) + PAD
-    cx = np.floor(xx.astype(np.float32) / ss32 + half).astype(int) + PAD
-    # slicing coordinates: FP64 (continuous)
-    zf = (g32.astype(np.float64) - float(lo32)) / float(sr32) + PAD
-    yf = yy / float(ss32) + PAD
-    xf = xx / float(ss32) + PAD
+    ss, sr = _params(sigma_s, sigma_r)
+    t, lo = grid_z_coords(g, sr)
+    hi = float(g.max())
+    gz, gy, gx = grid_shape(H, W, lo, hi, ss, sr)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    zc = np.floor(t)
+    if flip is not None:
+        zc = np.where(flip, _flipped_cell(t), zc)
+        gz = max(gz, int(zc.max()) + 1 + 2 * PAD)   # a flip upwards may need one more cell
+    cz = zc.astype(int) + PAD
+    cy = np.floor(yy / ss + 0.5).astype(int) + PAD
+    cx = np.floor(xx / ss + 0.5).astype(int) + PAD
+    zf = t - 0.5 + PAD
+    yf = yy / ss + PAD
+    xf = xx / ss + PAD
     wi = np.zeros((gz, gy, gx))
     w = np.zeros((gz, gy, gx))
     np.add.at(wi, (cz, cy, cx), g)
@@ -101,18 +133,24 @@ def blf_grid(g: np.ndarray, sigma_s: float, sigma_r: float) -> np.ndarray:
 
 
 def blfls_grid(img: np.ndarray, lam: float, sigma_s: float, sigma_r: float,
-               iters: int = 1) -> np.ndarray:
-    """BLF-LS with the grid BLF on each gradient field, then Eq. 8 (periodic solve)."""
+               iters: int = 1, flips: np.ndarray | None = None) -> np.ndarray:
+    """BLF-LS with the grid BLF on each gradient field, then Eq. 8 (periodic solve).
+    `flips` (bool [C][2][H][W], one pass only) marks, per channel and field (x, y), the pixels
+    whose range cell takes the other candidate."""
     a = np.asarray(img, dtype=np.float64)
     squeeze = a.ndim == 2
     if squeeze:
         a = a[None]
+    if flips is not None and int(iters) != 1:
+        raise ValueError("flips apply to one pass")
     u = a.copy()
     for _ in range(int(iters)):
         chans = []
         for c in range(u.shape[0]):
             gx, gy = gradients(u[c])
-            chans.append(solve_eq8(u[c], blf_grid(gx, sigma_s, sigma_r),
-                                   blf_grid(gy, sigma_s, sigma_r), lam))
+            fx = None if flips is None else flips[c][0]
+            fy = None if flips is None else flips[c][1]
+            chans.append(solve_eq8(u[c], blf_grid(gx, sigma_s, sigma_r, fx),
+                                   blf_grid(gy, sigma_s, sigma_r, fy), lam))
         u = np.stack(chans)
     return u[0] if squeeze else u

@@ -12,8 +12,9 @@
 //               (g, 1) to the range bin of each, in a fixed order (deterministic, no atomics);
 //   k6_blur     the 3-tap kernel (e^-1/2, 1, e^-1/2) along x, y, then z (zero outside);
 //   k6_slice    trilinear interpolation at (z, y / s_s + P, x / s_s + P): e = sum / count - g.
-// Cell indices are floor(t + 1/2) of FP32 quotients (IEEE division), the same decision the FP64
-// oracle takes in FP32.  Grid passes are HBM/L2-bound streams.
+// Cell indices are floor(t + 1/2) of the real t: FP32 decides away from rounding boundaries, FP64
+// near them (see cell_of), so the cells are those of the FP64 definition on the FP32 gradients.
+// Grid passes are HBM/L2-bound streams.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -82,9 +83,17 @@ struct GridGeom {
     int field;
 };
 
-__device__ __forceinline__ int cell_of(float num, float den)
+// floor((a - b) / den + 1/2) of the exact real value for FP32 operands: the FP32 evaluation
+// (relative error below 2.5e-7) decides when it lies more than 1e-6 (relative) away from both
+// neighbouring integers; otherwise FP64 decides (a - b exact, one correctly rounded division), so
+// a pixel near a rounding boundary goes where the FP64 definition puts it.
+__device__ __forceinline__ int cell_of(float a, float b, float den)
 {
-    return (int)floorf(__fdiv_rn(num, den) + 0.5f);
+    const float q = __fadd_rn(__fdiv_rn(__fsub_rn(a, b), den), 0.5f);
+    const float n = floorf(q);
+    const float margin = fmaxf(fabsf(q), 1.0f) * 1.0e-6f;
+    if (q - n > margin && (n + 1.0f) - q > margin) return (int)n;
+    return (int)floor(__dadd_rn(__ddiv_rn(__dsub_rn((double)a, (double)b), (double)den), 0.5));
 }
 
 // One thread per spatial cell (cy, cx) that a pixel can round to: floor((W-1)/s_s) + 2 cells per
@@ -103,11 +112,11 @@ __global__ void __launch_bounds__(kGridThreads) k6_splat(const float* __restrict
         const int x1 = min(G.W - 1, (int)ceilf((kx + 0.5f) * G.ss) + 1);
         float2* col = grid + (size_t)(ky + kPad) * G.gx + (kx + kPad);
         for (int y = y0; y <= y1; ++y) {
-            if (cell_of((float)y, G.ss) != ky) continue;
+            if (cell_of((float)y, 0.0f, G.ss) != ky) continue;
             for (int x = x0; x <= x1; ++x) {
-                if (cell_of((float)x, G.ss) != kx) continue;
+                if (cell_of((float)x, 0.0f, G.ss) != kx) continue;
                 const float g = grad_at(f, G.H, G.W, y, x, G.field);
-                const int z = cell_of(g - G.lo, G.sr) + kPad;
+                const int z = cell_of(g, G.lo, G.sr) + kPad;
                 float2* c = col + (size_t)z * slab;
                 c->x += g;
                 c->y += 1.f;

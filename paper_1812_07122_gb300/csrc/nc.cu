@@ -17,12 +17,15 @@
 // N iterations with r_k = sigma_s sqrt(3) 2^(N-k) / sqrt(4^N - 1) sqrt(3), rows then columns; the
 // last column pass writes the residual e = v - g for the Fourier solve.
 //
-// Exactness: a step is one FP32 multiply then one add (no fused multiply-add), capped at 2^20;
-// an FP32 value >= 1 is a multiple of 2^-23, so a step is an integer number of 2^-23 units and
-// sums of steps are exact in 64-bit integers in any order.  Steps are stored as 32-bit units
-// clamped to rq_1 + 1 (rq = floor(r 2^23), rq_1 that of the first, widest iteration): a run
-// containing a clamped step exceeds every radius either way, so no box decision changes.  The
-// box test is an integer comparison.
+// Box decisions follow the real-valued transform: a step 1 + a |dg| is formed from the exact
+// second difference of the FP32 image (error-free sums, so dg is exact) and a = sigma_s / sigma_r
+// (FP64, split into two FP32 words) as a double-float, and stored as a 32-bit integer number of
+// units of 2^-q rounded down, q the largest integer <= 30 with rq_1 + 1 < 2^32 (rq_k =
+// floor(r_k 2^q), r_k in FP64; rq_1 of the first, widest iteration).  Steps are clamped to
+// rq_1 + 1: a run containing such a step exceeds every radius either way.  Sums of steps are
+// exact in 64-bit integers in any order, and the box test "sum <= rq_k" differs from the exact
+// test "transform distance <= r_k" only when that distance lies within (number of steps) x 2^-q
+// of r_k.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -34,16 +37,42 @@ namespace blfls {
 namespace {
 
 constexpr int kNcThreads = 256;
-constexpr float kIncCap = 1048576.0f;      // 2^20
-constexpr float kUnit = 8388608.0f;        // 2^23
-
-// One step in units of 2^-23, clamped to `clamp` (exact: v 2^23 is an integer below 2^44).
-__device__ __forceinline__ unsigned step_units(float a, float cur, float prev,
-                                               unsigned long long clamp)
+// Error-free transformation: hi + lo == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo)
 {
-    const float v = fminf(__fadd_rn(1.0f, __fmul_rn(a, fabsf(cur - prev))), kIncCap);
-    const unsigned long long u = (unsigned long long)__float2ll_rz(v * kUnit);
-    return (unsigned)(u < clamp ? u : clamp);
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+
+// One step 1 + a |(p1 - p0) - (q1 - q0)| (the difference of two consecutive gradient samples,
+// each the difference of two image values), a = ah + al, in units of 2^-q (`scale` = 2^q) rounded
+// down and clamped to `clamp`.  The difference is exact as a double-float; the product and the
+// sum carry about 2^-46 relative error, the conversion less than one unit.
+__device__ __forceinline__ unsigned step_units(float p1, float p0, float q1, float q0, float ah,
+                                               float al, float scale, unsigned long long clamp)
+{
+    float d1h, d1l, d0h, d0l, dh, dl;
+    two_sum(p1, -p0, d1h, d1l);
+    two_sum(q1, -q0, d0h, d0l);
+    two_sum(d1h, -d0h, dh, dl);
+    dl = __fadd_rn(dl, __fsub_rn(d1l, d0l));
+    float nh, nl;
+    two_sum(dh, dl, nh, nl);                         // normalise
+    float ph = nh;
+    if (ph < 0.0f) { ph = -ph; nl = -nl; }
+    // m = a |d| as a double-float
+    const float mh = __fmul_rn(ah, ph);
+    const float ml = __fadd_rn(__fmaf_rn(ah, ph, -mh), __fmaf_rn(ah, nl, __fmul_rn(al, ph)));
+    // step = 1 + m
+    float sh, se;
+    two_sum(1.0f, mh, sh, se);
+    const float sl = __fadd_rn(se, ml);
+    const float xh = __fmul_rn(sh, scale), xl = __fmul_rn(sl, scale);   // exact scalings
+    if (xh >= (float)clamp) return (unsigned)clamp;
+    const float n = floorf(xh);
+    const long long u = (long long)n + (long long)floorf(__fadd_rn(__fsub_rn(xh, n), xl));
+    return (unsigned)(u < 0 ? 0 : ((unsigned long long)u < clamp ? u : (long long)clamp));
 }
 
 // g for both fields, and the steps of each field: sh_* between (y, x-1) and (y, x), sv_*
@@ -55,7 +84,7 @@ __global__ void __launch_bounds__(kNcThreads) k8_grad_steps(const float* __restr
                                                            unsigned* __restrict__ svx,
                                                            unsigned* __restrict__ shy,
                                                            unsigned* __restrict__ svy, int H,
-                                                           int W, float a,
+                                                           int W, float ah, float al, float scale,
                                                            unsigned long long clamp)
 {
     const size_t n = (size_t)H * W;
@@ -67,16 +96,15 @@ __global__ void __launch_bounds__(kNcThreads) k8_grad_steps(const float* __restr
         const float* r0 = f + (size_t)y * W;
         const float* ru = f + (size_t)yu * W;
         const float* rd = f + (size_t)yd * W;
-        const float c = r0[x];
-        const float gx0 = r0[xr] - c, gy0 = rd[x] - c;            // the fields at (y, x)
-        const float gxl = c - r0[xl], gyl = rd[xl] - r0[xl];      // at (y, x-1)
-        const float gxu = ru[xr] - ru[x], gyu = c - ru[x];        // at (y-1, x)
-        gx[i] = gx0;
-        gy[i] = gy0;
-        shx[i] = step_units(a, gx0, gxl, clamp);
-        svx[i] = step_units(a, gx0, gxu, clamp);
-        shy[i] = step_units(a, gy0, gyl, clamp);
-        svy[i] = step_units(a, gy0, gyu, clamp);
+        const float c = r0[x], cr = r0[xr], cl = r0[xl], cd = rd[x], cu = ru[x];
+        const float dl = rd[xl], ur = ru[xr];
+        gx[i] = cr - c;    // the fields at (y, x)
+        gy[i] = cd - c;
+        // steps between (y, x-1) and (y, x), and between (y-1, x) and (y, x), of each field
+        shx[i] = step_units(cr, c, c, cl, ah, al, scale, clamp);     // g_x(y,x) - g_x(y,x-1)
+        svx[i] = step_units(cr, c, ur, cu, ah, al, scale, clamp);    // g_x(y,x) - g_x(y-1,x)
+        shy[i] = step_units(cd, c, dl, cl, ah, al, scale, clamp);    // g_y(y,x) - g_y(y,x-1)
+        svy[i] = step_units(cd, c, c, cu, ah, al, scale, clamp);     // g_y(y,x) - g_y(y-1,x)
     }
 }
 
@@ -409,17 +437,21 @@ cudaError_t launch_nc_residuals(const float* f, float* ex, float* ey, int H, int
     unsigned* svx = shx + plane;
     unsigned* shy = svx + plane;
     unsigned* svy = shy + plane;
-    const float a = std::isfinite(sigma_r) ? sigma_s / sigma_r : 0.0f;   // FP32 division
-    std::vector<float> r(n_iter);
+    const double a = std::isfinite(sigma_r) ? (double)sigma_s / (double)sigma_r : 0.0;
+    const float ah = (float)a, al = (float)(a - (double)ah);
+    std::vector<double> r(n_iter);
     for (int k = 1; k <= n_iter; ++k)
-        r[k - 1] = (float)((double)sigma_s * std::sqrt(3.0) * std::pow(2.0, n_iter - k) /
-                           std::sqrt(std::pow(4.0, n_iter) - 1.0) * std::sqrt(3.0));
-    const auto units = [](float rk) { return (long long)std::floor((double)rk * 8388608.0); };
-    // r_1 is the widest radius; sigma_s <= BLFLS_MAX_NC_SIGMA_S keeps rq_1 + 1 below 2^32
+        r[k - 1] = (double)sigma_s * std::sqrt(3.0) * std::pow(2.0, n_iter - k) /
+                   std::sqrt(std::pow(4.0, n_iter) - 1.0) * std::sqrt(3.0);
+    // units of 2^-q: the largest q <= 30 with rq_1 + 1 < 2^32 (r_1 is the widest radius)
+    int q = 30;
+    while (q > 0 && std::floor(std::ldexp(r[0], q)) + 1.0 >= 4294967296.0) --q;
+    const auto units = [q](double rk) { return (long long)std::floor(std::ldexp(rk, q)); };
     const unsigned long long clamp = (unsigned long long)units(r[0]) + 1;
     if (clamp > 0xffffffffull) return cudaErrorInvalidValue;
     k8_grad_steps<<<nc_blocks(plane, num_sms), kNcThreads, 0, s>>>(f, gx, gy, shx, svx, shy, svy,
-                                                                  H, W, a, clamp);
+                                                                  H, W, ah, al, (float)std::ldexp(1.0, q),
+                                                                  clamp);
     for (int field = 0; field < 2; ++field) {
         const float* g = field == 0 ? gx : gy;
         const unsigned* sh = field == 0 ? shx : shy;

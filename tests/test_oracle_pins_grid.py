@@ -37,7 +37,8 @@ def test_grid_unit_spatial_step_single_range_bin_is_normalised_convolution():
 
 def test_grid_is_affine_equivariant():
     """(a g + b) with sigma_r scaled by a lands in the same cells: the output is a v + b.  The
-    values are dyadic and a is a power of two, so the FP32 cell decisions are exactly the same."""
+    values are dyadic and a is a power of two, so every cell coordinate is the same exact value
+    (some exactly on a rounding boundary, decided alike)."""
     g = _rng(2).integers(-16, 17, size=(20, 24)) / 64.0
     v = oracle.blf_grid(g, 2.0, 0.125)
     np.testing.assert_allclose(oracle.blf_grid(2.0 * g + 0.25, 2.0, 0.25), 2.0 * v + 0.25,
@@ -76,3 +77,23 @@ def test_grid_blfls_special_cases():
     np.testing.assert_allclose(u.sum(axis=(1, 2)), f.sum(axis=(1, 2)), rtol=1e-12)
     np.testing.assert_array_equal(oracle.blfls_grid(f, 20.0, 2.0, 0.1, iters=2),
                                   oracle.blfls_grid(u, 20.0, 2.0, 0.1))
+
+
+def test_a_flipped_cell_is_the_decision_just_across_the_boundary():
+    """A pixel whose range coordinate t is exactly an integer goes to cell t (floor(t + 1/2) of
+    the exact value); moving it to the other candidate cell equals lowering its value by a
+    hair, which puts t just below the boundary (the value itself changes by 1e-12)."""
+    g = _rng(5).integers(0, 32, size=(12, 14)) / 32.0
+    g[0, 0] = 0.0                      # min g = 0, so t = 4 g + 1/2: an integer where 32 g = 2 mod 4
+    sr = 0.125
+    t, lo = oracle.grid_z_coords(g, sr)
+    assert lo == 0.0
+    p = tuple(np.argwhere(np.abs(t - np.rint(t)) == 0)[0])   # a pixel exactly on a boundary
+    flip = np.zeros_like(g, dtype=bool)
+    flip[p] = True
+    got = oracle.blf_grid(g, 2.0, sr, flip)
+    h = g.copy()
+    h[p] -= 1e-12
+    want = oracle.blf_grid(h, 2.0, sr)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+    assert np.max(np.abs(got - oracle.blf_grid(g, 2.0, sr))) > 1e-4

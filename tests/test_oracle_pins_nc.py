@@ -23,42 +23,46 @@ def test_schedule_variances_sum_to_sigma_s_squared_and_halve():
 def test_domain_transform_by_hand():
     s = np.array([[0.0, 0.5, 0.5, 0.25]])
     ct, T = oracle.domain_transform(s, 2.0, axis=1)
-    # increments 1 + 2 |ds|: 2.0, 1.0, 1.5; wrap increment 1 + 2 |0 - 0.25| = 1.5 (all exact),
-    # held in integer units of 2^-23
-    np.testing.assert_array_equal(ct, np.array([[0.0, 2.0, 3.0, 4.5]]) * 2 ** 23)
-    np.testing.assert_array_equal(T, [6 * 2 ** 23])
+    # increments 1 + 2 |ds|: 2.0, 1.0, 1.5; wrap increment 1 + 2 |0 - 0.25| = 1.5 (all exact)
+    np.testing.assert_array_equal(ct, [[0.0, 2.0, 3.0, 4.5]])
+    np.testing.assert_array_equal(T, [6.0])
+    np.testing.assert_array_equal(oracle.increments(s, 2.0, axis=1), [[1.5, 2.0, 1.0, 1.5]])
 
 
-def test_domain_transform_is_the_exact_running_sum():
-    """Against exact rational arithmetic (Python fractions of the FP32 increments): no rounding
-    in the sum, whatever its length, and the cap on one huge step."""
+def test_transform_distances_are_exact_sums_of_the_increments():
+    """The distance a pass compares with r, against exact rational arithmetic: every margin
+    |ct(i + d) - ct(i)| - r equals the exact sum of 1 + a |s[j] - s[j-1]| over the steps between
+    i and i + d (periodic, several periods for a short line) minus r, to FP64 rounding."""
     from fractions import Fraction
-    s = _rng(4).normal(scale=0.4, size=(3, 500)).astype(np.float32)
-    s[1, 200] = 1e6                                  # 1 + a |ds| far above the cap of 2^20
-    a = np.float32(62.5)
-    ct, T = oracle.domain_transform(s, a, axis=1)
-    for row in range(3):
-        acc = Fraction(0)
-        for i in range(1, 500):
-            d = min(np.float32(1.0) + a * np.float32(abs(s[row, i] - s[row, i - 1])),
-                    np.float32(2.0 ** 20))
-            acc += Fraction(float(d))
-            assert Fraction(int(ct[row, i]), 2 ** 23) == acc
-        d = min(np.float32(1.0) + a * np.float32(abs(s[row, 0] - s[row, -1])), np.float32(2.0 ** 20))
-        assert Fraction(int(T[row]), 2 ** 23) == acc + Fraction(float(d))
+    s = _rng(4).normal(scale=0.4, size=(2, 9))
+    ss, sr = 3.0, 0.25
+    a = float(np.float32(ss)) / float(np.float32(sr))
+    r1 = oracle.nc_schedule(float(np.float32(ss)), 1)[0]
+    seen = 0
+    for k, axis, d, m in oracle.nc_margins(s, ss, sr, n_iter=1):
+        if axis != 1:
+            continue
+        for row in range(2):
+            for i in range(9):
+                acc = Fraction(0)
+                lo, hi = (i, i + d) if d > 0 else (i + d, i)
+                for j in range(lo + 1, hi + 1):
+                    acc += 1 + Fraction(a) * abs(Fraction(s[row, j % 9]) - Fraction(s[row, (j - 1) % 9]))
+                assert abs(Fraction(m[row, i]) - (acc - Fraction(r1))) <= Fraction(1, 2 ** 40)
+                seen += 1
+    assert seen == 2 * 9 * 2 * int(math.floor(r1))
 
 
 def _nc_pass_brute(v, ct, T, r):
     """Every sample of the previous, current and next period, scanned one by one (the inclusion
-    test written out with Python's exact integer-float comparison)."""
+    test written out on the FP64 running sum and period)."""
     n = v.size
     out = np.empty(n)
-    r32 = float(np.float32(r))
     for i in range(n):
         acc = cnt = 0.0
         for k in (-1, 0, 1):
             for j in range(n):
-                if abs(int(ct[j]) + k * int(T) - int(ct[i])) <= r32 * 2 ** 23:
+                if abs(ct[j] + k * T - ct[i]) <= r:
                     acc += v[j]
                     cnt += 1
         out[i] = acc / cnt
@@ -69,8 +73,25 @@ def _nc_pass_brute(v, ct, T, r):
 def test_nc_pass_matches_a_brute_force_scan(r):
     s = _rng(1).normal(scale=0.3, size=(1, 13))
     ct, T = oracle.domain_transform(s, 1.5, axis=1)
-    got = oracle.nc_pass(s, ct, T, r, axis=1)
+    got = oracle.nc_pass(s, oracle.increments(s, 1.5, axis=1), r, axis=1)
     np.testing.assert_allclose(got[0], _nc_pass_brute(s[0], ct[0], T[0], r), rtol=0, atol=1e-14)
+
+
+def test_a_flipped_decision_is_the_decision_at_a_slightly_other_radius():
+    """With r equal to one pair's transform distance, that pair is inside (<=) from both ends;
+    reversing those two decisions equals the pass at a radius a hair smaller, where only that
+    pair leaves."""
+    s = _rng(5).normal(scale=0.3, size=(1, 15))
+    inc = oracle.increments(s, 2.0, axis=1)
+    i0, d0 = 6, 2
+    r = float(inc[0, i0 + 1] + inc[0, i0 + 2])          # distance from 6 to 8
+    flip = {d0: np.zeros_like(s, dtype=bool), -d0: np.zeros_like(s, dtype=bool)}
+    flip[d0][0, i0] = True                               # 6 -> 8
+    flip[-d0][0, i0 + d0] = True                         # 8 -> 6
+    got = oracle.nc_pass(s, inc, r, axis=1, flip=flip)
+    want = oracle.nc_pass(s, inc, r * (1 - 1e-12), axis=1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+    assert np.max(np.abs(got - oracle.nc_pass(s, inc, r, axis=1))) > 1e-3
 
 
 def test_infinite_sigma_r_is_a_cascade_of_periodic_box_means():
