@@ -189,7 +189,9 @@ int blfls_smooth_normalized(blfls_handle *h, const float *img, float *out, int H
  * Eq. 1 (Paris and Durand's fast bilateral filter, which the paper's experiments use,
  * Sections III-A and IV): sampling steps sigma_s in space and sigma_r in range, a 2-cell zero
  * padding, splat to the nearest cell, 3-tap Gaussian blur of one cell along each grid axis,
- * trilinear slice; open image borders in the grid (the solve stays periodic).  FP32.  Device
+ * trilinear slice; open image borders in the grid (the solve stays periodic).  FP32; a pixel's
+ * cell is floor(t + 1/2) of the real value t of its coordinates for its FP32 gradient (taken in
+ * FP64 where the FP32 value is near a rounding boundary).  Device
  * pointers [C][H][W]; out may equal img.  Each pass reads the fields' ranges back to the host
  * to size the grid, so the call synchronises `stream` once per pass.  sigma_s must be finite and
  * >= 0.5; sigma_r may be +inf (one range cell).  Errors: BLFLS_EINVAL (arguments as
@@ -208,9 +210,13 @@ int blfls_smooth_grid(blfls_handle *h, const float *img, float *out, int H, int 
  * ct = running sum of 1 + (sigma_s / sigma_r) |g[j] - g[j-1]| along each row and each column
  * (periodic lines; computed once per pass from the unfiltered field), then nc_iters box
  * iterations of radius r_k = sigma_s sqrt(3) 2^(nc_iters-k) / sqrt(4^nc_iters - 1) sqrt(3) in the
- * transformed domain, rows then columns; then the Fourier solve of Eq. 8.  FP32 values; the
- * transform is exact (FP32 steps capped at 2^20, summed as integers in units of 2^-23), so the
- * set of samples in each box does not depend on rounding.  Device
+ * transformed domain, rows then columns; then the Fourier solve of Eq. 8.  FP32 values.  Each
+ * step of the transform is formed from the exact difference of the FP32 image's gradient samples
+ * as a double-float (a = sigma_s / sigma_r in FP64) and held as an integer number of units of
+ * 2^-q, rounded down, q the largest integer <= 30 with floor(r_1 2^q) + 1 < 2^32; sums of steps
+ * are exact, so the samples in a box do not depend on the order of any sum, and they are exactly
+ * those within r_k of its centre in the real-valued transform except where a distance lies
+ * within (its number of steps) x 2^-q of r_k.  Device
  * pointers [C][H][W], async; out may equal img.  sigma_s in (0, BLFLS_MAX_NC_SIGMA_S]; sigma_r
  * > 0 (+inf: plain box iterations); nc_iters in [1, BLFLS_MAX_NC_ITERS] (3 is the usual choice).
  * Errors: BLFLS_EINVAL, BLFLS_ENOMEM, BLFLS_ECUDA. */
@@ -246,6 +252,27 @@ typedef struct {
  * bad job fails the call with BLFLS_EINVAL before anything is enqueued.  Results equal those
  * of blfls_smooth on each job alone (same kernels, same arithmetic). */
 int blfls_smooth_batch(blfls_handle *h, const blfls_job *jobs, int n, void *stream);
+
+/* Served form on device buffers (the request loop around Eq. 7's solver): queue one job and
+ * return at once with a ticket.  The job's img and out are DEVICE pointers owned by the caller:
+ * img must already hold its data when blfls_submit is called (work that fills it must have
+ * completed, e.g. its stream synchronised), and neither buffer may be touched or freed until
+ * blfls_poll has reported the job done.  Jobs queued on a handle run in batches on the handle's
+ * own queue -- continuous batching: whenever one of its two streams is free, every queued job
+ * that fits (up to 64, within the queue's scratch budget) joins the next blfls_smooth_batch call,
+ * so jobs submitted while others run are admitted as those finish and batches overlap on the
+ * device.  The first call creates the queue: two internal handles with the calling handle's
+ * launch shapes, and scratch reserved up front (the calling handle's budget, or 8 GiB when it has
+ * none; a job that could never fit returns BLFLS_ENOMEM).  A job's result equals blfls_smooth on
+ * it alone.  Arguments are validated here (BLFLS_EINVAL, as blfls_smooth).  blfls_destroy
+ * cancels jobs not yet started and waits for running ones.  The queue is thread-safe: submit and
+ * poll may be called from any thread, unlike the handle's other calls. */
+int blfls_submit(blfls_handle *h, const blfls_job *job, uint64_t *ticket);
+/* *done = 0 while the job is queued or running, 1 once it has finished and out holds the result.
+ * The call that reports done also forgets the ticket (a later poll of it returns BLFLS_EINVAL);
+ * if the job failed, that call returns the job's error (BLFLS_ECUDA, ...) with *done = 1.
+ * Errors: BLFLS_EINVAL (NULL arguments, unknown ticket). */
+int blfls_poll(blfls_handle *h, uint64_t ticket, int *done);
 
 /* ---- Served form (no counterpart in the paper): continuous batching on one GPU ------------
  *
@@ -349,8 +376,10 @@ int blfls_pipe_rates(int device, double *rates, int n);
  *
  * The first call on a device sets up that device (looks up the static array's device address,
  * the SM count and the kernels' shared-memory limits); make that first call before any stream
- * capture begins on the device.  A call whose size differs from the previous call's copies new
- * FFT tables into the array from host memory, ordered on `stream`.
+ * capture begins on the device.  The array holds the FFT tables of one size pair at a time: a
+ * call whose size differs from the previous call's copies new tables into it from host memory,
+ * ordered on `stream`, replacing the old ones for every later kernel that reads them; such a call
+ * returns BLFLS_EINVAL and enqueues nothing while `stream` is capturing.
  * Every call shares the one array, which keeps the previous call's contents; each call
  * overwrites all of the scratch it reads.  Calls that overlap on the GPU (for example on two
  * streams of one device) race on the array: issue them on one stream, one after another.  The

@@ -90,6 +90,8 @@ _SIGNATURES = {
                                       _c_float, _vp]),
     "blfls_smooth_batch": (_c_int, [_vp, ctypes.POINTER(blfls_job), _c_int, _vp]),
     "blfls_profile_begin": (_c_int, [_vp, _c_int]),
+    "blfls_submit": (_c_int, [_vp, ctypes.POINTER(blfls_job), ctypes.POINTER(ctypes.c_uint64)]),
+    "blfls_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_c_int)]),
     "blfls_server_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _sz, _c_int, _c_int,
                                      ctypes.c_char_p]),
     "blfls_server_destroy": (None, [_vp]),
@@ -292,6 +294,20 @@ def make_job(img, out, H, W, C, lam, sigma_s, sigma_r, radius, iters=1, prec=BLF
 def blfls_smooth_batch(h, jobs, stream=None) -> None:
     arr = (blfls_job * len(jobs))(*jobs)
     _check(load().blfls_smooth_batch(h, arr, len(jobs), _stream(stream)), h)
+
+
+def blfls_submit(h, job) -> int:
+    """Queue one device-pointer job (see make_job) on the handle's queue; returns its ticket."""
+    t = ctypes.c_uint64()
+    _check(load().blfls_submit(h, ctypes.byref(job), ctypes.byref(t)), h)
+    return t.value
+
+
+def blfls_poll(h, ticket) -> bool:
+    """True once the job has finished (the ticket is then forgotten); raises if it failed."""
+    d = ctypes.c_int()
+    _check(load().blfls_poll(h, ctypes.c_uint64(ticket), ctypes.byref(d)), h)
+    return bool(d.value)
 
 
 def blfls_autotune(h, H, W, C, radius, prec=BLFLS_FP32, table_path: str | None = None) -> None:

@@ -438,6 +438,12 @@ static int smooth_host_pipelined(blfls_handle* h, const float* img_host, float* 
     return BLFLS_OK;
 }
 
+// The queue behind blfls_submit: two slots (batches on two streams overlap), batches of up to
+// 64 jobs, scratch from the handle's budget or 8 GiB when the handle has none.
+constexpr size_t kSubmitDefaultBudget = (size_t)8 << 30;
+constexpr int kSubmitSlots = 2;
+constexpr int kSubmitMaxBatch = 64;
+
 extern "C" {
 
 int blfls_create(blfls_handle** out, int device, size_t mem_budget_bytes,
@@ -474,6 +480,7 @@ int blfls_create(blfls_handle** out, int device, size_t mem_budget_bytes,
 void blfls_destroy(blfls_handle* h)
 {
     if (!h) return;
+    blfls_server_destroy(h->submit_srv);   // cancels queued jobs, finishes running ones
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
     for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
@@ -1019,6 +1026,35 @@ int blfls_smooth_batch(blfls_handle* h, const blfls_job* jobs, int n, void* stre
     DeviceGuard g(h->device);
     if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
     return run_batch(h, jobs, n, static_cast<cudaStream_t>(stream));
+}
+
+int blfls_submit(blfls_handle* h, const blfls_job* job, uint64_t* ticket)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    const NvtxRange range("blfls_submit");
+    blfls_server* srv;
+    {
+        std::lock_guard<std::mutex> lock(h->submit_mu);
+        if (!h->submit_srv) {
+            const size_t budget = h->budget ? h->budget : kSubmitDefaultBudget;
+            const int rc = create_job_server(&h->submit_srv, h, budget, kSubmitSlots, kSubmitMaxBatch);
+            if (rc != BLFLS_OK) return rc;
+        }
+        srv = h->submit_srv;
+    }
+    return server_submit_job(srv, job, ticket);
+}
+
+int blfls_poll(blfls_handle* h, uint64_t ticket, int* done)
+{
+    if (!h) return fail(BLFLS_EINVAL, "handle is NULL");
+    blfls_server* srv;
+    {
+        std::lock_guard<std::mutex> lock(h->submit_mu);
+        srv = h->submit_srv;
+    }
+    if (!srv) return fail(BLFLS_EINVAL, "unknown ticket (nothing was submitted)");
+    return server_poll_job(srv, ticket, done);
 }
 
 int blfls_profile_begin(blfls_handle* h, int max_events)

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,10 @@ struct blfls_handle {
     std::map<std::pair<int, int>, int> tune_tile_h;
     std::map<int, int> tune_col_block;
     blfls::BatchState* batch = nullptr;
+    // blfls_submit / blfls_poll: a continuous-batching queue of device-pointer jobs with its own
+    // slot handles and streams, created by the first blfls_submit
+    blfls_server* submit_srv = nullptr;
+    std::mutex submit_mu;   // guards the queue's creation
 };
 
 namespace blfls {
@@ -106,6 +111,14 @@ int reserve_batch_scratch(blfls_handle* h, size_t bytes);
 int tuned_tile_h(const blfls_handle* h, int radius, int prec);
 int tuned_col_block(const blfls_handle* h, int L);
 int load_tune_table(blfls_handle* h, const char* path);
+// The queue behind blfls_submit / blfls_poll (serve.cu): a server without a host-buffer arena
+// whose `slots` slot handles share `budget` bytes of scratch and take h's launch shapes.
+int create_job_server(blfls_server** out, const blfls_handle* h, size_t budget, int slots,
+                      int max_batch);
+int server_submit_job(blfls_server* S, const blfls_job* j, uint64_t* ticket);
+// *done = 1 once the job has finished (the record is then forgotten; its error, if it failed,
+// is returned), 0 while it is queued or running.
+int server_poll_job(blfls_server* S, uint64_t ticket, int* done);
 int save_tune_table(const blfls_handle* h, const char* path);
 
 }  // namespace blfls

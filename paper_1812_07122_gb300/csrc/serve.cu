@@ -1,8 +1,9 @@
 // Served form of BLF-LS: a continuous-batching request loop on one GPU (no counterpart in the
 // paper).
 //
-// Requests arrive with host buffers (blfls_server_submit returns a ticket at once).  A scheduler
-// thread keeps
+// Requests arrive with host buffers (blfls_server_submit returns a ticket at once), or -- for the
+// handle-level blfls_submit / blfls_poll -- as jobs on device buffers the caller owns, which
+// skip the arena and the copies.  A scheduler thread keeps
 //   * an arena: one device allocation made at creation, from which every request's input and
 //     output buffers are carved (first fit, coalescing on release) -- resident memory, so the
 //     steady state makes no cudaMalloc or cudaFree;
@@ -115,7 +116,9 @@ private:
 
 struct Request {
     uint64_t id = 0;
-    blfls_request r{};
+    blfls_request r{};   // parameters (and host buffers unless device_io)
+    bool device_io = false;
+    blfls_job job{};     // device buffers of a device-pointer job
     double t_submit = 0, t_admit = 0, t_done = 0;
     std::atomic<int> status{0};    // 0 queued, 3 running, 1 done, 2 cancelled, < 0 error
     size_t off_in = SIZE_MAX, off_out = SIZE_MAX;
@@ -221,6 +224,17 @@ std::vector<Request*> select_batch(blfls_server* S)
             ++it;
             continue;
         }
+        if (q->device_io) {   // the caller's device buffers: nothing to carve
+            int expected = 0;
+            if (!q->status.compare_exchange_strong(expected, 3)) {
+                it = S->pending.erase(it);
+                continue;
+            }
+            scratch += q->scratch;
+            batch.push_back(q);
+            it = S->pending.erase(it);
+            continue;
+        }
         const size_t in = S->arena.alloc(io_bytes(q->r));
         if (in == SIZE_MAX) {
             ++it;
@@ -259,6 +273,10 @@ void launch_batch(blfls_server* S, Slot* slot, const std::vector<Request*>& batc
     int rc = BLFLS_OK;
     for (Request* q : batch) {
         q->t_admit = t;
+        if (q->device_io) {
+            jobs.push_back(q->job);
+            continue;
+        }
         float* din = reinterpret_cast<float*>(S->arena.at(q->off_in));
         float* dout = reinterpret_cast<float*>(S->arena.at(q->off_out));
         if (cudaMemcpyAsync(din, q->r.img_host, io_bytes(q->r), cudaMemcpyHostToDevice, slot->s) != cudaSuccess)
@@ -269,6 +287,7 @@ void launch_batch(blfls_server* S, Slot* slot, const std::vector<Request*>& batc
     if (rc == BLFLS_OK) rc = blfls_smooth_batch(slot->h, jobs.data(), (int)jobs.size(), slot->s);
     if (rc == BLFLS_OK) {
         for (Request* q : batch) {
+            if (q->device_io) continue;
             if (cudaMemcpyAsync(q->r.out_host, S->arena.at(q->off_out), io_bytes(q->r),
                                 cudaMemcpyDeviceToHost, slot->s) != cudaSuccess)
                 rc = BLFLS_ECUDA;
@@ -324,10 +343,14 @@ void scheduler(blfls_server* S)
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int blfls_server_create(blfls_server** out, int device, size_t mem_budget_bytes, int slots,
-                        int max_batch, const char* tune_table_path)
+// Server with `arena_pct` percent of the budget for request buffers (0: device-pointer jobs
+// only), the rest split 7:1 between the slots' batch scratch and their plans and tables; the
+// slot handles take their launch shapes from `tune_from` when given.
+int create_server(blfls_server** out, int device, size_t mem_budget_bytes, int slots,
+                  int max_batch, const char* tune_table_path, int arena_pct,
+                  const blfls_handle* tune_from)
 {
     if (!out) return fail(BLFLS_EINVAL, "out is NULL");
     *out = nullptr;
@@ -340,21 +363,30 @@ int blfls_server_create(blfls_server** out, int device, size_t mem_budget_bytes,
     S->device = device;
     S->budget = mem_budget_bytes;
     S->max_batch = max_batch;
-    // budget split: 60% I/O arena, 35% the slots' batch scratch, 5% their plans and tables
-    const size_t arena_bytes = align_up(mem_budget_bytes / 100 * 60, 256);
-    S->slot_scratch = mem_budget_bytes / 100 * 35 / slots;
-    const size_t slot_extra = mem_budget_bytes / 100 * 5 / slots;
-    cudaError_t e = cudaMalloc(&S->arena_mem, arena_bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete S;
-        return fail(BLFLS_ENOMEM, std::string("server arena: ") + cudaGetErrorString(e));
+    // budget split: arena_pct% I/O arena, the rest 7:1 between the slots' batch scratch and their
+    // plans and tables (60 / 35 / 5 for host-buffer requests)
+    const size_t arena_bytes = align_up(mem_budget_bytes / 100 * arena_pct, 256);
+    const size_t rest = mem_budget_bytes / 100 * (100 - arena_pct);
+    S->slot_scratch = rest / 8 * 7 / slots;
+    const size_t slot_extra = rest / 8 / slots;
+    if (arena_bytes) {
+        cudaError_t e = cudaMalloc(&S->arena_mem, arena_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete S;
+            return fail(BLFLS_ENOMEM, std::string("server arena: ") + cudaGetErrorString(e));
+        }
     }
     S->arena.init(static_cast<unsigned char*>(S->arena_mem), arena_bytes);
     for (int i = 0; i < slots; ++i) {
         Slot* slot = new Slot();
         slot->srv = S;
         int rc = blfls_create(&slot->h, device, S->slot_scratch + slot_extra, tune_table_path);
+        if (rc == BLFLS_OK && tune_from) {
+            slot->h->tune_tile_h = tune_from->tune_tile_h;
+            slot->h->tune_col_block = tune_from->tune_col_block;
+            slot->h->col_block = tune_from->col_block;
+        }
         if (rc == BLFLS_OK) rc = reserve_batch_scratch(slot->h, S->slot_scratch);
         if (rc == BLFLS_OK && cudaStreamCreateWithFlags(&slot->s, cudaStreamNonBlocking) != cudaSuccess)
             rc = BLFLS_ECUDA;
@@ -365,7 +397,7 @@ int blfls_server_create(blfls_server** out, int device, size_t mem_budget_bytes,
                 if (sl->h) blfls_destroy(sl->h);
                 delete sl;
             }
-            cudaFree(S->arena_mem);
+            if (S->arena_mem) cudaFree(S->arena_mem);
             delete S;
             return rc;
         }
@@ -373,6 +405,78 @@ int blfls_server_create(blfls_server** out, int device, size_t mem_budget_bytes,
     S->thread = std::thread(scheduler, S);
     *out = S;
     return BLFLS_OK;
+}
+
+}  // namespace
+
+namespace blfls {
+
+int create_job_server(blfls_server** out, const blfls_handle* h, size_t budget, int slots,
+                      int max_batch)
+{
+    return create_server(out, h->device, budget, slots, max_batch, nullptr, 0, h);
+}
+
+int server_submit_job(blfls_server* S, const blfls_job* j, uint64_t* ticket)
+{
+    if (!S || !j || !ticket) return fail(BLFLS_EINVAL, "NULL argument");
+    int rc;
+    if ((rc = check_image_args(j->img, j->out, j->H, j->W, j->C)) != BLFLS_OK) return rc;
+    if ((rc = check_blf_args(j->H, j->W, j->sigma_s, j->sigma_r, j->radius, j->prec)) != BLFLS_OK) return rc;
+    if ((rc = check_lambda(j->lambda)) != BLFLS_OK) return rc;
+    if (j->iters < 0 || j->iters > BLFLS_MAX_ITERS) return fail(BLFLS_EINVAL, "iters out of range");
+    Request* q = new Request();
+    q->device_io = true;
+    q->job = *j;
+    q->r = blfls_request{nullptr, nullptr, j->H, j->W, j->C, j->lambda, j->sigma_s, j->sigma_r,
+                         j->radius, j->iters, j->prec};
+    q->scratch = scratch_bytes(q->r);
+    q->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (q->scratch > S->slot_scratch) {
+            S->rejected++;
+            delete q;
+            return fail(BLFLS_ENOMEM, "job larger than the submit queue's scratch budget allows");
+        }
+        q->id = S->next_id++;
+        if (S->first_submit < 0) S->first_submit = q->t_submit;
+        S->all[q->id] = q;
+        S->incoming.push_back(q);
+        S->submitted++;
+        *ticket = q->id;
+    }
+    S->cv.notify_all();
+    return BLFLS_OK;
+}
+
+int server_poll_job(blfls_server* S, uint64_t ticket, int* done)
+{
+    if (!S || !done) return fail(BLFLS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(BLFLS_EINVAL, "unknown ticket");
+    const int st = it->second->status.load();
+    if (st == 0 || st == 3) {
+        *done = 0;
+        return BLFLS_OK;
+    }
+    *done = 1;
+    delete it->second;   // reported once: the record is forgotten
+    S->all.erase(it);
+    if (st < 0) return fail(st, "job failed");
+    return BLFLS_OK;
+}
+
+}  // namespace blfls
+
+extern "C" {
+
+int blfls_server_create(blfls_server** out, int device, size_t mem_budget_bytes, int slots,
+                        int max_batch, const char* tune_table_path)
+{
+    return create_server(out, device, mem_budget_bytes, slots, max_batch, tune_table_path, 60,
+                         nullptr);
 }
 
 void blfls_server_destroy(blfls_server* S)

@@ -86,6 +86,8 @@ def test_job_struct_matches_the_header():
     ("blfls_solve_residual", (1, 1, 1, 1, 8, 8, 1, 1.0, None)),
     ("blfls_smooth_batch", (None, 0, None)),
     ("blfls_profile_begin", (16,)),
+    ("blfls_submit", (None, None)),
+    ("blfls_poll", (1, None)),
 ])
 def test_every_entry_point_rejects_a_null_handle_on_the_host(lib, name, args):
     """Argument checks run on the host before anything touches the GPU: a NULL handle is

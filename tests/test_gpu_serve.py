@@ -128,3 +128,44 @@ def test_cancel_a_queued_request():
             blfls.blfls_server_poll(srv, tickets[0])      # released: unknown ticket
     finally:
         blfls.blfls_server_destroy(srv)
+
+
+def test_handle_submit_poll_equals_smooth_bit_for_bit(h):
+    """blfls_submit / blfls_poll on the handle (device-pointer jobs, continuous batching on the
+    handle's own queue): every result equals blfls_smooth on the job alone, bit for bit, the
+    ticket is forgotten once reported done, and invalid jobs are refused at submit."""
+    import time
+
+    import torch
+
+    from gpu_util import DEV, to_dev
+
+    reqs = _make(24, seed=3)
+    q = blfls.blfls_create(0)
+    try:
+        ins = [to_dev(f) for f, _ in reqs]
+        outs = [torch.full_like(x, float("nan")) for x in ins]
+        torch.cuda.synchronize(DEV)       # the inputs hold their data before the jobs are queued
+        tickets = []
+        for (f, p), x, o in zip(reqs, ins, outs):
+            job = blfls.make_job(x, o, p["H"], p["W"], p["C"], p["lam"], p["ss"], p["sr"], p["r"])
+            tickets.append(blfls.blfls_submit(q, job))
+        pending = set(tickets)
+        deadline = time.monotonic() + 120
+        while pending and time.monotonic() < deadline:
+            pending = {t for t in pending if not blfls.blfls_poll(q, t)}
+            time.sleep(0.001)
+        assert not pending, f"{len(pending)} jobs unfinished"
+        with pytest.raises(blfls.BlflsError) as ei:
+            blfls.blfls_poll(q, tickets[0])           # reported done once: forgotten
+        assert ei.value.code == blfls.BLFLS_EINVAL
+        bad = blfls.make_job(ins[0], outs[0], 8, 8, 1, -1.0, 1.0, 0.1, 1)
+        with pytest.raises(blfls.BlflsError) as ei:
+            blfls.blfls_submit(q, bad)
+        assert ei.value.code == blfls.BLFLS_EINVAL
+        got = [o.cpu().numpy() for o in outs]
+    finally:
+        blfls.blfls_destroy(q)
+    for (f, p), g in zip(reqs, got):
+        alone = smooth(h, f, p["lam"], p["ss"], p["sr"], p["r"], 1)
+        assert np.array_equal(g, alone), p
