@@ -153,17 +153,28 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def cpu_oracle_sample(f, rows: int | None, threads: int):
+def cpu_oracle_sample(f, rows: int | None, threads: int, keep: list | None = None):
     """Time the FP64 oracle on channel 0, one pass, rows [0, rows) (all rows if None).
-    Returns (seconds, fraction of the whole workload's work that the sample covers)."""
+    Returns (seconds, fraction of the whole workload's work that the sample covers); the
+    result is appended to `keep` when given."""
     import oracle
     f0 = f[0] if rows is None else f[0, :rows]
     t0 = time.perf_counter()
-    oracle.blfls_channel(f0, PARAMS["lam"], PARAMS["sigma_s"], PARAMS["sigma_r"],
-                         PARAMS["radius"], threads)
+    u = oracle.blfls_channel(f0, PARAMS["lam"], PARAMS["sigma_s"], PARAMS["sigma_r"],
+                             PARAMS["radius"], threads)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.append(u)
     frac = (f0.shape[0] * f0.shape[1]) / (H * W) / C / PARAMS["iters"]
     return dt, frac
+
+
+def channel_errors(a, b) -> dict:
+    """Per-channel max-abs and RMS of a - b (arrays [C][H][W]), in FP64."""
+    import numpy as np
+    d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
+    return {"max_abs": [float(f"{v:.3e}") for v in np.abs(d).max(axis=(1, 2))],
+            "rms": [float(f"{v:.3e}") for v in np.sqrt((d * d).mean(axis=(1, 2)))]}
 
 
 def run_reference(args):
@@ -515,13 +526,23 @@ def main():
 
     # precision forms on the same workload
     forms = None
+    one_pass = {}      # precision -> this workload's image after ONE pass (for the oracle errors)
     if not args.no_forms:
         forms = {}
+        full = {}
         for name, prec in [("fp32", 0), ("fp16w", 1), ("bf16w", 2)]:
             try:
                 forms[name] = timed_mp(lambda: step(prec), max(3, K // 4))
+                full[name] = out.cpu().numpy()
+                blfls.blfls_smooth(h, x, out, H, W, C, p["lam"], p["sigma_s"], p["sigma_r"],
+                                   p["radius"], 1, prec, stream)
+                one_pass[name] = out.cpu().numpy()
             except blfls.BlflsError as e:
                 forms[name] = f"unavailable: {e}"
+        # per-channel error of the reduced-precision forms against the plain FP32 path on the
+        # whole workload (3 passes, every pixel); against the FP64 oracle below (one pass)
+        forms["errors_vs_fp32_path"] = {k: channel_errors(full[k], full["fp32"])
+                                        for k in ("fp16w", "bf16w") if k in full and "fp32" in full}
 
     # the LS model (Eq. 6) and the base/detail applications on the same image and parameters
     modes = None
@@ -593,7 +614,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = oracle.default_threads()
-        dt, frac = cpu_oracle_sample(f, None, threads)
+        kept = []
+        dt, frac = cpu_oracle_sample(f, None, threads, kept)
         cpu = {"value": round(mp / (dt / frac), 4), "unit": "MP/s", "cores": threads,
                "kind": "oracle",
                "sample": f"channel 0, one pass, whole 3840x2160 plane ({dt:.1f} s; "
@@ -610,6 +632,14 @@ def main():
         cpu["one_core"] = {"value": round(mp / (dt1 / frac1), 5), "unit": "MP/s", "cores": 1,
                            "sample": f"channel 0, one pass, rows 0-134 ({dt1:.1f} s; "
                                      f"{frac1:.5f} of the workload), scaled"}
+        if forms is not None and one_pass:
+            # precision report against the FP64 oracle: one pass of every channel of the 4K
+            # image (channel 0 from the timed sample above; the others untimed)
+            ref = [kept[0]] + [oracle.blfls_channel(f[c], p["lam"], p["sigma_s"], p["sigma_r"],
+                                                    p["radius"], threads) for c in range(1, C)]
+            ref = np.stack(ref)
+            forms["errors_vs_fp64_oracle_one_pass"] = {k: channel_errors(v, ref)
+                                                       for k, v in one_pass.items()}
         cpu["small_workload"] = {"workload": "256x256 grey rectangles, radius 5, one pass",
                                  "all_cores_s": round(c1_all, 3), "one_core_s": round(c1_one, 3),
                                  "all_cores_mp_per_s": round(0.065536 / c1_all, 4),

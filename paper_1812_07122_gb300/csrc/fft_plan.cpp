@@ -137,99 +137,20 @@ bool fill_stage_division(FftPlanDev& d)
 cudaError_t build_fft_plan(int N, FftPlanHost& out)
 {
     out = FftPlanHost{};
-    FftPlanDev& d = out.dev;
-    d.N = N;
-    std::vector<int> radices;
-    const bool direct = factor_direct(N, radices);
-    int L = N;
-    if (!direct) {
-        L = bluestein_length(N);
-        if (!factor_direct(L, radices)) return cudaErrorInvalidValue;
-    }
-    if (L > kMaxFftLen) return cudaErrorInvalidValue;
-    d.L = L;
-    d.bluestein = direct ? 0 : 1;
-    d.nst = int(radices.size());
-    for (int s = 0; s < d.nst; ++s) d.radix[s] = radices[s];
-    if (!fill_stage_division(d) || !fill_padding(d)) return cudaErrorInvalidValue;
-
-    // Host tables.
-    std::vector<float2> tw(L);
-    for (int m = 0; m < L; ++m) {
-        const double ang = -2.0 * kPi * double(m) / double(L);
-        tw[m] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
-    }
-    const std::vector<int> posL = dif_positions(L, radices);
-    std::vector<int> iperm(L);
-    for (int k = 0; k < L; ++k) iperm[posL[k]] = k;
-    std::vector<int> perm(N);
-    std::vector<float2> chirp, bhat;
-    if (direct) {
-        perm = posL;
-    } else {
-        for (int k = 0; k < N; ++k) perm[k] = k;
-        for (int p = 0; p < L; ++p) iperm[p] = p;
-        // c_n = exp(-i pi n^2 / N), with n^2 reduced mod 2N in integers to keep the angle exact.
-        std::vector<std::complex<double>> c(N);
-        chirp.resize(N);
-        for (int n = 0; n < N; ++n) {
-            const long long q = (long long)n * n % (2LL * N);
-            const double ang = -kPi * double(q) / double(N);
-            c[n] = std::complex<double>(std::cos(ang), std::sin(ang));
-            chirp[n] = make_float2(float(c[n].real()), float(c[n].imag()));
-        }
-        std::vector<std::complex<double>> b(L, 0.0);
-        for (int n = 0; n < N; ++n) {
-            b[n] = std::conj(c[n]);
-            if (n > 0) b[L - n] = std::conj(c[n]);
-        }
-        host_fft_smooth(b);
-        bhat.resize(L);
-        for (int k = 0; k < L; ++k) {
-            const std::complex<double> v = b[k] / double(L);
-            bhat[posL[k]] = make_float2(float(v.real()), float(v.imag()));
-        }
-    }
-
-    std::vector<float> lap(N);
-    for (int k = 0; k < N; ++k) {
-        const double sn = std::sin(kPi * double(k) / double(N));
-        lap[k] = float(4.0 * sn * sn);
-    }
-
-    // One device allocation: tw | chirp | bhat | perm | iperm | lap.
-    const size_t o_tw = 0;
-    const size_t o_chirp = align256(o_tw + sizeof(float2) * L);
-    const size_t o_bhat = align256(o_chirp + sizeof(float2) * chirp.size());
-    const size_t o_perm = align256(o_bhat + sizeof(float2) * bhat.size());
-    const size_t o_iperm = align256(o_perm + sizeof(int) * N);
-    const size_t o_lap = align256(o_iperm + sizeof(int) * L);
-    const size_t bytes = align256(o_lap + sizeof(float) * N);
-    std::vector<unsigned char> host(bytes, 0);
-    std::memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * L);
-    if (!chirp.empty()) std::memcpy(host.data() + o_chirp, chirp.data(), sizeof(float2) * N);
-    if (!bhat.empty()) std::memcpy(host.data() + o_bhat, bhat.data(), sizeof(float2) * L);
-    std::memcpy(host.data() + o_perm, perm.data(), sizeof(int) * N);
-    std::memcpy(host.data() + o_iperm, iperm.data(), sizeof(int) * L);
-    std::memcpy(host.data() + o_lap, lap.data(), sizeof(float) * N);
-
+    std::vector<unsigned char> blob;
+    FftPlanDev rel;
+    if (!build_fft_tables_host(N, blob, rel)) return cudaErrorInvalidValue;
     void* dmem = nullptr;
-    cudaError_t e = cudaMalloc(&dmem, bytes);
+    cudaError_t e = cudaMalloc(&dmem, blob.size());
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(dmem, host.data(), bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dmem, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dmem);
         return e;
     }
-    unsigned char* base = static_cast<unsigned char*>(dmem);
-    d.tw = reinterpret_cast<const float2*>(base + o_tw);
-    d.chirp = chirp.empty() ? nullptr : reinterpret_cast<const float2*>(base + o_chirp);
-    d.bhat = bhat.empty() ? nullptr : reinterpret_cast<const float2*>(base + o_bhat);
-    d.perm = reinterpret_cast<const int*>(base + o_perm);
-    d.iperm = reinterpret_cast<const int*>(base + o_iperm);
-    d.lap = reinterpret_cast<const float*>(base + o_lap);
+    out.dev = bind_fft_tables(rel, dmem);
     out.dmem = dmem;
-    out.bytes = bytes;
+    out.bytes = blob.size();
     return cudaSuccess;
 }
 
@@ -239,9 +160,12 @@ void free_fft_plan(FftPlanHost& p)
     p = FftPlanHost{};
 }
 
-// The same tables as build_fft_plan, laid out in one host blob instead of a device allocation.
-// `rel` receives the plan with every table pointer holding its byte offset inside the blob;
-// bind_fft_tables turns those offsets into addresses once the blob sits at `base`.
+// Every table of the plan of length N (twiddles, digit-reversal positions, Bluestein chirp and
+// kernel spectrum, Laplacian eigenvalues), computed in FP64 and stored FP32, laid out in one host
+// blob: tw | chirp | bhat | perm | iperm | lap, each 256-byte aligned.  `rel` receives the plan
+// with every table pointer holding its byte offset inside the blob; bind_fft_tables turns those
+// offsets into addresses once the blob sits at `base` (build_fft_plan uploads it to its own
+// allocation, the allocation-free solve into its static array).
 bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& rel)
 {
     rel = FftPlanDev{};
@@ -275,6 +199,7 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     } else {
         for (int k = 0; k < N; ++k) perm[k] = k;
         for (int p = 0; p < L; ++p) iperm[p] = p;
+        // c_n = exp(-i pi n^2 / N), with n^2 reduced mod 2N in integers to keep the angle exact.
         std::vector<std::complex<double>> c(N);
         chirp.resize(N);
         for (int n = 0; n < N; ++n) {

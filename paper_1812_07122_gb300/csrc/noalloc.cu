@@ -105,7 +105,15 @@ extern "C" int blfls_solve_residual_noalloc(const float* img, const float* ex, c
     unsigned char* spec = slot.base;
     unsigned char* tables = slot.base + kSpecBytes;
     if (slot.rows_n != W || slot.cols_n != H) {
-        // Upload the tables of this size pair; stream-ordered after earlier work on `s`.
+        // Upload the tables of this size pair; stream-ordered after earlier work on `s`.  The
+        // copy reads pageable host memory, which a stream capture cannot record: refuse it
+        // there rather than break the capture.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(s, &cap);
+        if (e != cudaSuccess) return fail(BLFLS_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(BLFLS_EINVAL, "no-allocation solve: this size needs new FFT tables, which "
+                                      "cannot be uploaded while the stream is capturing");
         e = cudaMemcpyAsync(tables, rt->blob.data(), rt->blob.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(tables + rt->blob.size(), ct->blob.data(), ct->blob.size(),
