@@ -120,14 +120,27 @@ __host__ __device__ __forceinline__ size_t tile_smem_bytes(int R, size_t elem, i
     return f_bytes(R, th) + 2 * elem * (size_t)g_rows(R, th) * g_pitch(R);
 }
 
+// The image tile with its periodic halo: rows y0 - R .., columns x0 - R .. (fr x fp values).
+// Each warp takes whole tile rows with its lanes along the row (coalesced loads); a lane wraps
+// its columns once and a warp each of its rows once, instead of wrapping every element.
+constexpr int kTileColsPerLane = (kTW + 2 * kMaxTiledR + 1 + 31) / 32;
+
 __device__ __forceinline__ void load_f_tile(const float* __restrict__ f, int H, int W, int x0,
                                             int y0, int R, int th, float* sf)
 {
     const int fp = f_pitch(R), fr = f_rows(R, th);
-    for (int i = threadIdx.x; i < fr * fp; i += blockDim.x) {
-        const int r = i / fp, c = i - r * fp;
-        const int yy = wrap_idx(y0 - R + r, H), xx = wrap_idx(x0 - R + c, W);
-        sf[i] = __ldg(f + (size_t)yy * W + xx);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int xs[kTileColsPerLane];
+#pragma unroll
+    for (int k = 0; k < kTileColsPerLane; ++k) xs[k] = wrap_idx(x0 - R + lane + 32 * k, W);
+    for (int r = threadIdx.x >> 5; r < fr; r += nw) {
+        const float* row = f + (size_t)wrap_idx(y0 - R + r, H) * W;
+        float* srow = sf + r * fp;
+#pragma unroll
+        for (int k = 0; k < kTileColsPerLane; ++k) {
+            const int c = lane + 32 * k;
+            if (c < fp) srow[c] = __ldg(row + xs[k]);
+        }
     }
 }
 

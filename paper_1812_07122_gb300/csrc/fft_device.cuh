@@ -110,6 +110,21 @@ __device__ __forceinline__ void dft4_at(float2 (&v)[N], int o, int st)
     v[o + 3 * st] = csub(b, d);
 }
 
+// a * w16^e (e = 0..15, sign of the transform); the roots +-1 and +-i as a swap and signs.
+template <bool INV>
+__device__ __forceinline__ float2 mul_w16(float2 a, int e)
+{
+    e &= 15;
+    if (e == 0) return a;
+    if ((e & 3) == 0) {
+        // exp(-+i pi e / 8) = (-+i)^(e / 4)
+        const int quad = e >> 2;
+        if (quad == 2) return make_float2(-a.x, -a.y);
+        return (quad == 1) != INV ? rot_i<false>(a) : rot_i<true>(a);
+    }
+    return cmul(a, w16<INV>(e));
+}
+
 // In-register R-point DFT, y_q = sum_t x_t w^(t q), w = exp(-+2 pi i / R).
 template <int R, bool INV>
 __device__ __forceinline__ void small_dft(float2 (&v)[R])
@@ -126,7 +141,7 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R])
         dft4_at<INV>(v, 0, 2);
         dft4_at<INV>(v, 1, 2);
 #pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1) v[2 * k1 + 1] = cmul(v[2 * k1 + 1], w16<INV>(2 * k1));
+        for (int k1 = 1; k1 < 4; ++k1) v[2 * k1 + 1] = mul_w16<INV>(v[2 * k1 + 1], 2 * k1);
         float2 y[8];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
@@ -144,7 +159,7 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R])
 #pragma unroll
         for (int k1 = 1; k1 < 4; ++k1)
 #pragma unroll
-            for (int t2 = 1; t2 < 4; ++t2) v[4 * k1 + t2] = cmul(v[4 * k1 + t2], w16<INV>(k1 * t2));
+            for (int t2 = 1; t2 < 4; ++t2) v[4 * k1 + t2] = mul_w16<INV>(v[4 * k1 + t2], k1 * t2);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) dft4_at<INV>(v, 4 * k1, 1);
         float2 y[16];
@@ -571,6 +586,106 @@ __device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* _
         }
     }
     __syncthreads();
+}
+
+// Butterfly geometry of stage (R, M) of a compile-time plan, for drivers that move a
+// butterfly's data between global memory, staging buffers and registers themselves (the first
+// and last stages of a transform) instead of through ct_stage.  Butterfly b covers column
+// `col` (b mod 2^LGC) and the natural positions nat + t M, t = 0..R-1; its elements sit at buffer
+// offsets off + t st.  fwd / inv apply the butterfly and its twiddles in registers exactly as
+// ct_stage does (same operations, same results).
+template <int R, int M, int L, int LGC, int PADS>
+struct CtStage {
+    using B = typename Bfly<R>::type;
+    static constexpr unsigned total = (unsigned)(L / R) << LGC;   // butterflies of all columns
+    static constexpr unsigned mask = (1u << LGC) - 1u;
+    static constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : ((unsigned)M << LGC);
+    static constexpr unsigned tw_step = (unsigned)(L / (M * R));
+    static __device__ __forceinline__ void locate(unsigned b, unsigned& nat, unsigned& j,
+                                                  unsigned& col)
+    {
+        col = b & mask;
+        const unsigned bi = b >> LGC;
+        const unsigned blk = bi / (unsigned)M;
+        j = bi - blk * (unsigned)M;
+        nat = blk * (unsigned)M * R + j;
+    }
+    static __device__ __forceinline__ unsigned offset(unsigned nat, unsigned col)
+    {
+        unsigned base = nat;
+        if constexpr (PADS > 0) base += base / (unsigned)PADS;
+        return (base << LGC) + col;
+    }
+    // forward (decimation in frequency): v in input order t -> out[q] = DFT(v)_q w^(j q)
+    static __device__ __forceinline__ void fwd(float2 (&v)[R], float2 (&out)[R],
+                                               const float2* __restrict__ tw, unsigned j)
+    {
+        B::template dft<false>(v);
+        if constexpr (M > 1) {
+            float2 w[R];
+            twiddle_powers<R, B::F>(w, tw, j * tw_step);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const float2 y = v[B::slot(q)];
+                out[q] = q ? cmul(y, w[q]) : y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) out[q] = v[B::slot(q)];
+        }
+    }
+    // inverse: a in output order q -> out[t] = IDFT(a conj(w^(j q)))_t
+    static __device__ __forceinline__ void inv(float2 (&a)[R], float2 (&out)[R],
+                                               const float2* __restrict__ tw, unsigned j)
+    {
+        float2 v[R];
+        if constexpr (M > 1) {
+            float2 w[R];
+            twiddle_powers<R, B::F>(w, tw, j * tw_step);
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = q ? cmulc(a[q], w[q]) : a[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = a[q];
+        }
+        B::template dft<true>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[t] = v[B::slot(t)];
+    }
+};
+
+// Frequency held at work position p after the forward transform of plan P (the digit reversal:
+// p = sum_s q_s span(s)  <->  k = sum_s q_s R_0 ... R_{s-1}); the same as the plan's iperm table.
+template <class P, int... S>
+__device__ __forceinline__ int ct_frequency_digits(unsigned p, std::integer_sequence<int, S...>)
+{
+    int k = 0, w = 1;
+    ((k += (int)(p / (unsigned)P::span(S)) * w, p %= (unsigned)P::span(S), w *= P::radix[S]), ...);
+    return k;
+}
+template <class P>
+__device__ __forceinline__ int ct_frequency(unsigned p)
+{
+    return ct_frequency_digits<P>(p, std::make_integer_sequence<int, P::nst>{});
+}
+
+// Stage s of plan P as a CtStage.
+template <class P, int S, int LGC, int PADS>
+using CtStageOf = CtStage<P::radix[S], P::span(S), P::L, LGC, PADS>;
+
+// Middle stages [S0, S1) of plan P through shared memory (forward, in order).
+template <class P, int LGC, int PADS, int S0, int... S>
+__device__ __forceinline__ void ct_forward_range(float2* x, const float2* tw,
+                                                 std::integer_sequence<int, S...>)
+{
+    (ct_stage<P::radix[S0 + S], P::span(S0 + S), P::L, LGC, PADS, false>(x, tw), ...);
+}
+// Inverse stages S1-1 .. S0 of plan P through shared memory (in the inverse order).
+template <class P, int LGC, int PADS, int S1, int... S>
+__device__ __forceinline__ void ct_inverse_range(float2* x, const float2* tw,
+                                                 std::integer_sequence<int, S...>)
+{
+    (ct_stage<P::radix[S1 - 1 - S], P::span(S1 - 1 - S), P::L, LGC, PADS, true>(x, tw), ...);
 }
 
 template <class P, int LGC, int PADS, int... S>

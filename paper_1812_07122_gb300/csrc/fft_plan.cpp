@@ -162,7 +162,7 @@ void free_fft_plan(FftPlanHost& p)
 
 // Every table of the plan of length N (twiddles, digit-reversal positions, Bluestein chirp and
 // kernel spectrum, Laplacian eigenvalues), computed in FP64 and stored FP32, laid out in one host
-// blob: tw | chirp | bhat | perm | iperm | lap, each 256-byte aligned.  `rel` receives the plan
+// blob: tw | chirp | bhat | perm | iperm | lap | lapp, each 256-byte aligned.  `rel` receives the plan
 // with every table pointer holding its byte offset inside the blob; bind_fft_tables turns those
 // offsets into addresses once the blob sits at `base` (build_fft_plan uploads it to its own
 // allocation, the allocation-free solve into its static array).
@@ -230,8 +230,11 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     const size_t o_bhat = align256(o_chirp + sizeof(float2) * chirp.size());
     const size_t o_perm = align256(o_bhat + sizeof(float2) * bhat.size());
     const size_t o_iperm = align256(o_perm + sizeof(int) * N);
+    std::vector<float> lapp(L);
+    for (int p = 0; p < L; ++p) lapp[p] = lap[iperm[p] % N];
     const size_t o_lap = align256(o_iperm + sizeof(int) * L);
-    const size_t bytes = align256(o_lap + sizeof(float) * N);
+    const size_t o_lapp = align256(o_lap + sizeof(float) * N);
+    const size_t bytes = align256(o_lapp + sizeof(float) * L);
     blob.assign(bytes, 0);
     std::memcpy(blob.data() + o_tw, tw.data(), sizeof(float2) * L);
     if (!chirp.empty()) std::memcpy(blob.data() + o_chirp, chirp.data(), sizeof(float2) * N);
@@ -239,12 +242,14 @@ bool build_fft_tables_host(int N, std::vector<unsigned char>& blob, FftPlanDev& 
     std::memcpy(blob.data() + o_perm, perm.data(), sizeof(int) * N);
     std::memcpy(blob.data() + o_iperm, iperm.data(), sizeof(int) * L);
     std::memcpy(blob.data() + o_lap, lap.data(), sizeof(float) * N);
+    std::memcpy(blob.data() + o_lapp, lapp.data(), sizeof(float) * L);
     rel.tw = reinterpret_cast<const float2*>(o_tw);
     rel.chirp = chirp.empty() ? nullptr : reinterpret_cast<const float2*>(o_chirp);
     rel.bhat = bhat.empty() ? nullptr : reinterpret_cast<const float2*>(o_bhat);
     rel.perm = reinterpret_cast<const int*>(o_perm);
     rel.iperm = reinterpret_cast<const int*>(o_iperm);
     rel.lap = reinterpret_cast<const float*>(o_lap);
+    rel.lapp = reinterpret_cast<const float*>(o_lapp);
     return true;
 }
 
@@ -258,6 +263,7 @@ FftPlanDev bind_fft_tables(const FftPlanDev& rel, const void* base)
     d.perm = reinterpret_cast<const int*>(b + reinterpret_cast<size_t>(rel.perm));
     d.iperm = reinterpret_cast<const int*>(b + reinterpret_cast<size_t>(rel.iperm));
     d.lap = reinterpret_cast<const float*>(b + reinterpret_cast<size_t>(rel.lap));
+    d.lapp = reinterpret_cast<const float*>(b + reinterpret_cast<size_t>(rel.lapp));
     return d;
 }
 

@@ -37,6 +37,7 @@ struct FftPlanDev {
     const float2* bhat;    // L entries (Bluestein): DFT_L of the conjugate chirp / L, in the
                            // direct transform's position order
     const float* lap;      // N entries: 4 sin^2(pi k / N), the periodic Laplacian's eigenvalues
+    const float* lapp;     // L entries: lap[iperm[p] mod N], the eigenvalue at work position p
     // Row buffers place work position p at p + p / S, S = pad_span = L / radix[0] (direct plans
     // of two or more stages; 0 = no padding), so that positions S apart (the digit-reversed
     // neighbours k, k+1) fall in different shared-memory banks.

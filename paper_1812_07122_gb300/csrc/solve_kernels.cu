@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_staged(const float2
 }
 
 // Launched with any block size up to kColThreadsMax (chosen per plan, see col_threads).
-constexpr int kColThreadsMax = 576;
+constexpr int kColThreadsMax = 768;   // keeps 85 registers per thread available
 
 template <int LGC, class P>
 __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restrict__ spec, int H,
@@ -524,6 +524,282 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_staged(float2* __restr
             if (kx < Wh) spec[(size_t)n * Wh + kx] = data[i];
         }
         __syncthreads();
+    }
+}
+
+// ---- single image, compile-time plans, fused stage endpoints --------------------------------
+// The same transforms as the staged drivers, operation for operation (bit-identical results),
+// with the first and last stages moving their data between registers and global memory or the
+// staging buffers directly, so shared memory sees only the exchanges between stages:
+//   K2: each first-stage butterfly forms its inputs r = D_x^T e_x + D_y^T e_y from the staged rows
+//       in registers (no build pass);
+//   K3: the first stage reads the spectrum from global memory, the last forward stage, the
+//       spectral divide and the first inverse stage run in registers (one butterfly, no exchange
+//       between them), and the last inverse stage writes the spectrum back (no staging buffer,
+//       so more CTAs fit on an SM);
+//   K4: the first inverse stage gathers its inputs straight from the staged half spectra
+//       (Hermitian rebuild in registers) and the last one writes u = f + result.
+
+template <class P>
+__global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* __restrict__ ex,
+                                                                   const float* __restrict__ ey,
+                                                                   float2* __restrict__ spec,
+                                                                   int H, int W, FftPlanDev rp,
+                                                                   int vec)
+{
+    static_assert(P::nst >= 2, "fused drivers need two or more stages");
+    constexpr int PADS = P::L / P::radix[0];
+    constexpr int R0 = P::radix[0];
+    constexpr unsigned M0 = P::span(0);
+    using S0 = CtStageOf<P, 0, 0, PADS>;
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    float* st = reinterpret_cast<float*>(staged_smem);
+    const size_t Wp = row_floats(W);
+    float2* data = reinterpret_cast<float2*>(staged_smem + k2s_stage_bytes(W));
+    const int Wh = W / 2 + 1;
+    const int npairs = (H + 1) / 2;
+    int p0, p1;
+    band(npairs, p0, p1);
+    if (p0 >= p1) return;
+    auto issue = [&](int p) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const int ym = (y0 == 0) ? H - 1 : y0 - 1;
+        stage_floats(st, ex + (size_t)y0 * W, W, vec);
+        stage_floats(st + 2 * Wp, ey + (size_t)ym * W, W, vec);
+        stage_floats(st + 3 * Wp, ey + (size_t)y0 * W, W, vec);
+        if (y1 < H) {
+            stage_floats(st + Wp, ex + (size_t)y1 * W, W, vec);
+            stage_floats(st + 4 * Wp, ey + (size_t)y1 * W, W, vec);
+        }
+        cp_commit();
+    };
+    const float* ex0 = st;
+    const float* ex1 = st + Wp;
+    const float* eym = st + 2 * Wp;
+    const float* ey0 = st + 3 * Wp;
+    const float* ey1 = st + 4 * Wp;
+    issue(p0);
+    for (int p = p0; p < p1; ++p) {
+        cp_wait<0>();
+        __syncthreads();
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const bool has1 = y1 < H;
+        for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
+            unsigned nat, j, col;
+            S0::locate(b, nat, j, col);
+            float2 v[R0];
+#pragma unroll
+            for (int t = 0; t < R0; ++t) {
+                const int x = (int)(nat + t * M0);
+                const int xm = (x == 0) ? W - 1 : x - 1;
+                // (D_x^T e_x)[x] = e_x[x-1] - e_x[x];  (D_y^T e_y)[y] = e_y[y-1] - e_y[y]
+                const float r0 = (ex0[xm] - ex0[x]) + (eym[x] - ey0[x]);
+                const float r1 = has1 ? (ex1[xm] - ex1[x]) + (ey0[x] - ey1[x]) : 0.f;
+                v[t] = make_float2(r0, r1);
+            }
+            float2 o[R0];
+            S0::fwd(v, o, rp.tw, j);
+            float2* xb = data + S0::offset(nat, col);
+#pragma unroll
+            for (int q = 0; q < R0; ++q) xb[q * S0::st] = o[q];
+        }
+        __syncthreads();
+        if (p + 1 < p1) issue(p + 1);   // the rows of pair p have been read out
+        ct_forward_range<P, 0, PADS, 1>(data, rp.tw, std::make_integer_sequence<int, P::nst - 1>{});
+        float2* s0 = spec + (size_t)y0 * Wh;
+        float2* s1 = spec + (size_t)(has1 ? y1 : y0) * Wh;
+#pragma unroll 4
+        for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
+            const int kn = (k == 0) ? 0 : W - k;
+            const float2 zk = data[row_pos(rp, __ldg(rp.perm + k))];
+            const float2 zn = data[row_pos(rp, __ldg(rp.perm + kn))];
+            // A = (Z_k + conj Z_{W-k}) / 2,  B = (Z_k - conj Z_{W-k}) / (2i)
+            s0[k] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            if (has1) s1[k] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+        }
+        __syncthreads();
+    }
+}
+
+template <int LGC, class P>
+__global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restrict__ spec, int H,
+                                                                int W, FftPlanDev cp,
+                                                                const float* __restrict__ sx,
+                                                                float lam, float scale)
+{
+    static_assert(P::nst >= 2, "fused drivers need two or more stages");
+    constexpr int R0 = P::radix[0];
+    constexpr unsigned M0 = P::span(0);
+    constexpr int NL = P::nst - 1;
+    constexpr int RL = P::radix[NL];
+    using S0 = CtStageOf<P, 0, LGC, 0>;
+    using SL = CtStageOf<P, NL, LGC, 0>;
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    float2* data = reinterpret_cast<float2*>(staged_smem);
+    constexpr int CB = 1 << LGC;
+    const int Wh = W / 2 + 1;
+    const int nblk = (Wh + CB - 1) >> LGC;
+    const float2* tw = cp.tw;
+    int b0, b1;
+    band(nblk, b0, b1);
+    for (int blk = b0; blk < b1; ++blk) {
+        const int kx0 = blk * CB;
+        // first forward stage, inputs from the spectrum in global memory
+        for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
+            unsigned nat, j, col;
+            S0::locate(b, nat, j, col);
+            const int kx = kx0 + (int)col;
+            float2 v[R0];
+#pragma unroll
+            for (int t = 0; t < R0; ++t)
+                v[t] = kx < Wh ? spec[(size_t)(nat + t * M0) * Wh + kx] : make_float2(0.f, 0.f);
+            float2 o[R0];
+            S0::fwd(v, o, tw, j);
+            float2* xb = data + S0::offset(nat, col);
+#pragma unroll
+            for (int q = 0; q < R0; ++q) xb[q * S0::st] = o[q];
+        }
+        __syncthreads();
+        ct_forward_range<P, LGC, 0, 1>(data, tw, std::make_integer_sequence<int, NL - 1>{});
+        // last forward stage, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the
+        // 1/(HW) of the inverse), first inverse stage -- all in registers
+        for (unsigned b = threadIdx.x; b < SL::total; b += blockDim.x) {
+            unsigned nat, j, col;
+            SL::locate(b, nat, j, col);
+            float2* xb = data + SL::offset(nat, col);
+            float2 v[RL], y[RL], o[RL];
+#pragma unroll
+            for (int t = 0; t < RL; ++t) v[t] = xb[t * SL::st];
+            SL::fwd(v, y, tw, j);
+            const float sxv = __ldg(sx + min(kx0 + (int)col, Wh - 1));
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const float syv = __ldg(cp.lapp + nat + q);
+                const float den = fmaf(lam, sxv + syv, 1.0f);
+                const float m = __fdividef(scale, den) * lam;
+                y[q] = make_float2(y[q].x * m, y[q].y * m);
+            }
+            SL::inv(y, o, tw, j);
+#pragma unroll
+            for (int t = 0; t < RL; ++t) xb[t * SL::st] = o[t];
+        }
+        __syncthreads();
+        ct_inverse_range<P, LGC, 0, NL>(data, tw, std::make_integer_sequence<int, NL - 1>{});
+        // last inverse stage, outputs to the spectrum in global memory
+        for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
+            unsigned nat, j, col;
+            S0::locate(b, nat, j, col);
+            const int kx = kx0 + (int)col;
+            const float2* xb = data + S0::offset(nat, col);
+            float2 a[R0], o[R0];
+#pragma unroll
+            for (int q = 0; q < R0; ++q) a[q] = xb[q * S0::st];
+            S0::inv(a, o, tw, j);
+            if (kx < Wh) {
+#pragma unroll
+                for (int t = 0; t < R0; ++t) spec[(size_t)(nat + t * M0) * Wh + kx] = o[t];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2* __restrict__ spec,
+                                                                   const float* f, float* out,
+                                                                   int H, int W, FftPlanDev rp,
+                                                                   int vec)
+{
+    static_assert(P::nst >= 2, "fused drivers need two or more stages");
+    constexpr int PADS = P::L / P::radix[0];
+    constexpr int R0 = P::radix[0];
+    constexpr unsigned M0 = P::span(0);
+    constexpr int NL = P::nst - 1;
+    constexpr int RL = P::radix[NL];
+    using S0 = CtStageOf<P, 0, 0, PADS>;
+    using SL = CtStageOf<P, NL, 0, PADS>;
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    const int Wh = W / 2 + 1;
+    const size_t Wp = row_floats(W);
+    float2* ss = reinterpret_cast<float2*>(staged_smem);
+    float* sf = reinterpret_cast<float*>(staged_smem + k4s_spec_bytes(W));
+    float2* data = reinterpret_cast<float2*>(staged_smem + k4s_spec_bytes(W) + sizeof(float) * 2 * Wp);
+    const int npairs = (H + 1) / 2;
+    int p0, p1;
+    band(npairs, p0, p1);
+    if (p0 >= p1) return;
+    auto issue_spec = [&](int p) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        stage_complex(ss, spec + (size_t)y0 * Wh, Wh);
+        if (y1 < H) stage_complex(ss + Wh, spec + (size_t)y1 * Wh, Wh);
+        cp_commit();
+    };
+    auto issue_f = [&](int p) {
+        const int y0 = 2 * p, y1 = y0 + 1;
+        stage_floats(sf, f + (size_t)y0 * W, W, vec);
+        if (y1 < H) stage_floats(sf + Wp, f + (size_t)y1 * W, W, vec);
+        cp_commit();
+    };
+    // Copy groups complete in issue order: spectra(p), f(p), spectra(p+1), f(p+1), ...
+    issue_spec(p0);
+    issue_f(p0);
+    for (int p = p0; p < p1; ++p) {
+        cp_wait<1>();                 // spectra(p) landed; f(p) may still be in flight
+        __syncthreads();
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const bool has1 = y1 < H;
+        // first inverse stage (the last stage's inverse, span 1), its inputs Z = A + i B rebuilt
+        // from the two half spectra by Hermitian symmetry at the frequencies of its positions.
+        // Butterfly b = q0 (L / (R0 R_last)) + rest holds frequencies whose lowest digit is q0, so
+        // thread i takes q0 = i mod R0: adjacent lanes read adjacent frequencies of the staged
+        // spectra (no bank conflicts), and write positions L / R0 apart (padded: no conflicts).
+        for (unsigned i = threadIdx.x; i < SL::total; i += blockDim.x) {
+            const unsigned b = (i % (unsigned)R0) * (SL::total / (unsigned)R0) + i / (unsigned)R0;
+            unsigned nat, j, col;
+            SL::locate(b, nat, j, col);
+            float2 v[RL], o[RL];
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const int k = ct_frequency<P>(nat + q);
+                const bool upper = k > W / 2;
+                const int kk = upper ? W - k : k;
+                float2 a = ss[kk];
+                float2 bb = has1 ? ss[Wh + kk] : make_float2(0.f, 0.f);
+                if (upper) { a.y = -a.y; bb.y = -bb.y; }
+                if (k == 0 || 2 * k == W) { a.y = 0.f; bb.y = 0.f; }  // real bins of a real row
+                v[q] = make_float2(a.x - bb.y, a.y + bb.x);            // Z = A + i B
+            }
+            SL::inv(v, o, rp.tw, j);
+            float2* xb = data + SL::offset(nat, col);
+#pragma unroll
+            for (int t = 0; t < RL; ++t) xb[t * SL::st] = o[t];
+        }
+        __syncthreads();
+        const bool more = p + 1 < p1;
+        if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
+        ct_inverse_range<P, 0, PADS, NL>(data, rp.tw, std::make_integer_sequence<int, NL - 1>{});
+        if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
+        __syncthreads();
+        // last inverse stage (stage 0): u = f + result, real part row a, imaginary part row b
+        float* o0 = out + (size_t)y0 * W;
+        float* o1 = out + (size_t)(has1 ? y1 : y0) * W;
+        for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
+            unsigned nat, j, col;
+            S0::locate(b, nat, j, col);
+            const float2* xb = data + S0::offset(nat, col);
+            float2 a[R0], z[R0];
+#pragma unroll
+            for (int q = 0; q < R0; ++q) a[q] = xb[q * S0::st];
+            S0::inv(a, z, rp.tw, j);
+#pragma unroll
+            for (int t = 0; t < R0; ++t) {
+                const int x = (int)(nat + t * M0);
+                o0[x] = sf[x] + z[t].x;
+                if (has1) o1[x] = sf[Wp + x] + z[t].y;
+            }
+        }
+        __syncthreads();
+        if (more) issue_f(p + 1);
     }
 }
 
@@ -799,14 +1075,14 @@ static bool plan_is(const FftPlanDev& p)
 
 static RowsK2Fn rows_k2_kernel(const FftPlanDev& rp)
 {
-    if (plan_is<RowPlanA>(rp)) return k2_rows_staged<RowPlanA>;
-    if (plan_is<RowPlanB>(rp)) return k2_rows_staged<RowPlanB>;
+    if (plan_is<RowPlanA>(rp)) return k2_rows_fused<RowPlanA>;
+    if (plan_is<RowPlanB>(rp)) return k2_rows_fused<RowPlanB>;
     return k2_rows_staged<void>;
 }
 static RowsK4Fn rows_k4_kernel(const FftPlanDev& rp)
 {
-    if (plan_is<RowPlanA>(rp)) return k4_rows_staged<RowPlanA>;
-    if (plan_is<RowPlanB>(rp)) return k4_rows_staged<RowPlanB>;
+    if (plan_is<RowPlanA>(rp)) return k4_rows_fused<RowPlanA>;
+    if (plan_is<RowPlanB>(rp)) return k4_rows_fused<RowPlanB>;
     return k4_rows_staged<void>;
 }
 
@@ -821,33 +1097,56 @@ static ColsStagedFn cols_staged_kernel_p(int lgc)
         default: return k3_cols_staged<4, P>;   // col_block is at most 16
     }
 }
+typedef void (*ColsFusedFn)(float2*, int, int, FftPlanDev, const float*, float, float);
+template <class P>
+static ColsFusedFn cols_fused_kernel_p(int lgc)
+{
+    switch (lgc) {
+        case 0: return k3_cols_fused<0, P>;
+        case 1: return k3_cols_fused<1, P>;
+        case 2: return k3_cols_fused<2, P>;
+        case 3: return k3_cols_fused<3, P>;
+        default: return k3_cols_fused<4, P>;
+    }
+}
+// The fused column driver of a compile-time plan, or nullptr (runtime plans: staged driver).
+static ColsFusedFn cols_fused_kernel(int lgc, const FftPlanDev& cp)
+{
+    if (plan_is<ColPlanA>(cp)) return cols_fused_kernel_p<ColPlanA>(lgc);
+    if (plan_is<ColPlanB>(cp)) return cols_fused_kernel_p<ColPlanB>(lgc);
+    return nullptr;
+}
 static ColsStagedFn cols_staged_kernel(int lgc, const FftPlanDev& cp)
 {
-    if (plan_is<ColPlanA>(cp)) return cols_staged_kernel_p<ColPlanA>(lgc);
-    if (plan_is<ColPlanB>(cp)) return cols_staged_kernel_p<ColPlanB>(lgc);
+    (void)cp;
     return cols_staged_kernel_p<void>(lgc);
 }
+// Shared memory of the fused column driver: one column block.
+static size_t k3f_smem(int L, int lgc) { return sizeof(float2) * ((size_t)L << lgc); }
 
 static void set_staged_attributes()
 {
     const int big = 227 * 1024;
-    for (RowsK2Fn f : {k2_rows_staged<void>, k2_rows_staged<RowPlanA>, k2_rows_staged<RowPlanB>})
+    for (RowsK2Fn f : {k2_rows_staged<void>, k2_rows_fused<RowPlanA>, k2_rows_fused<RowPlanB>})
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    for (RowsK4Fn f : {k4_rows_staged<void>, k4_rows_staged<RowPlanA>, k4_rows_staged<RowPlanB>})
+    for (RowsK4Fn f : {k4_rows_staged<void>, k4_rows_fused<RowPlanA>, k4_rows_fused<RowPlanB>})
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    for (int lgc = 0; lgc <= 4; ++lgc)
-        for (ColsStagedFn f : {cols_staged_kernel_p<void>(lgc), cols_staged_kernel_p<ColPlanA>(lgc),
-                               cols_staged_kernel_p<ColPlanB>(lgc)})
+    for (int lgc = 0; lgc <= 4; ++lgc) {
+        cudaFuncSetAttribute(cols_staged_kernel_p<void>(lgc),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        for (ColsFusedFn f : {cols_fused_kernel_p<ColPlanA>(lgc), cols_fused_kernel_p<ColPlanB>(lgc)})
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    }
 }
 
-static int col_threads(const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
+// Block size of a column driver (fn: its kernel); see the comment above.
+static int col_threads(const void* fn, const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
 {
     int best_t = 128, best_occ = 1;
     double best = 1e30;
     for (int t = 128; t <= kColThreadsMax; t += 32) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cols_staged_kernel(lgc, cp), t, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem);
         if (occ < 1) continue;
         long rounds = 0;
         for (int st = 0; st < cp.nst; ++st) {
@@ -875,8 +1174,11 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
                                         reinterpret_cast<uintptr_t>(f)) % 16 == 0);
     const bool rows_staged = k2s_smem(W, rp) <= cap && k4s_smem(W, rp) <= cap;
     int lgc = solve_fit_lgc(cp.L, p.col_block);
-    while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
-    const bool cols_staged = k3s_smem(cp.L, lgc) <= cap;
+    const ColsFusedFn k3f = cols_fused_kernel(lgc, cp);
+    if (!k3f)
+        while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
+    const bool cols_fused = k3f != nullptr && k3f_smem(cp.L, lgc) <= cap;
+    const bool cols_staged = !cols_fused && k3s_smem(cp.L, lgc) <= cap;
     const int CB = 1 << lgc;
     const int npairs = (H + 1) / 2;
     const int nblk = (W / 2 + 1 + CB - 1) / CB;
@@ -898,12 +1200,19 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
         k2_rows_forward<<<grid_r, thr_r, smem_r, s>>>(ex, ey, spec, H, W, rp, tw_r);
     }
     if (marks) cudaEventRecord(marks[0], s);
-    if (cols_staged) {
+    if (cols_fused) {
+        const size_t sm3 = k3f_smem(cp.L, lgc);
+        int occ = 0;
+        const int thr = col_threads((const void*)k3f, cp, lgc, sm3, &occ);
+        const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
+        k3f<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, p.lambda, scale);
+    } else if (cols_staged) {
         const size_t sm3 = k3s_smem(cp.L, lgc);
         int occ = 0;
-        const int thr = col_threads(cp, lgc, sm3, &occ);
+        const ColsStagedFn k3 = cols_staged_kernel(lgc, cp);
+        const int thr = col_threads((const void*)k3, cp, lgc, sm3, &occ);
         const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
-        cols_staged_kernel(lgc, cp)<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
+        k3<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
     } else {
         const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
         const int CB1 = 1 << lgc1;
