@@ -481,6 +481,158 @@ __device__ __forceinline__ void bluestein(float2* x, int lgc, const FftPlanDev& 
     __syncthreads();
 }
 
+// ---- Bluestein with its pointwise passes folded into the stages ---------------------------
+// The same values as `bluestein` (operation for operation), in 2 nst - 1 passes over shared
+// memory instead of 2 nst + 3: the chirp pre-multiply (and the zero padding beyond N) is taken in
+// the loads of the first forward stage, the multiply by the kernel spectrum between the last
+// forward stage and the first inverse stage (one butterfly, in registers: that stage has span 1),
+// and the chirp post-multiply in the stores of the last inverse stage.  Plans of two or more
+// stages (a one-stage plan takes `bluestein`).
+
+template <class F>
+__device__ __forceinline__ void with_radix(int R, F&& f)
+{
+    switch (R) {
+        case 16: f(OneLevel<16>{}); break;
+        case 15: f(TwoLevel<3, 5>{}); break;
+        case 9: f(TwoLevel<3, 3>{}); break;
+        case 8: f(OneLevel<8>{}); break;
+        case 4: f(OneLevel<4>{}); break;
+        case 2: f(OneLevel<2>{}); break;
+        case 3: f(OneLevel<3>{}); break;
+        case 5: f(OneLevel<5>{}); break;
+        default: f(OneLevel<7>{}); break;
+    }
+}
+
+// Forward stage 0 with the chirp in its loads: input n is conj^INV(x_n) c_n for n < N, 0 beyond.
+template <class B, bool INV>
+__device__ __forceinline__ void blue_first_stage(float2* __restrict__ x, int lgc,
+                                                 const FftPlanDev& p, const float2* __restrict__ tw)
+{
+    constexpr int R = B::R;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned m = (unsigned)p.span[0];
+    const unsigned total = (unsigned)(p.L / R) << lgc;
+    const unsigned st = m << lgc;
+    const unsigned N = (unsigned)p.N;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned j = b >> lgc;                       // stage 0: one block, base = j
+        float2* xb = x + ((j << lgc) + col);
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const unsigned n = j + t * m;
+            float2 a = make_float2(0.f, 0.f);
+            if (n < N) {
+                a = xb[t * st];
+                if (INV) a = cconj(a);
+                a = cmul(a, __ldg(p.chirp + n));
+            }
+            v[t] = a;
+        }
+        B::template dft<false>(v);
+        float2 w[R];
+        twiddle_powers<R, B::F>(w, tw, j);                 // tw_step of stage 0 is 1
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 y = v[B::slot(q)];
+            xb[q * st] = q ? cmul(y, w[q]) : y;
+        }
+    }
+    __syncthreads();
+}
+
+// Last forward stage (span 1), times the kernel spectrum, then its inverse.
+template <class B>
+__device__ __forceinline__ void blue_middle_stage(float2* __restrict__ x, int lgc,
+                                                  const FftPlanDev& p)
+{
+    constexpr int R = B::R;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned total = (unsigned)(p.L / R) << lgc;
+    const unsigned st = 1u << lgc;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned base = (b >> lgc) * R;
+        float2* xb = x + ((base << lgc) + col);
+        float2 v[R], a[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = xb[t * st];
+        B::template dft<false>(v);
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = cmul(v[B::slot(q)], __ldg(p.bhat + base + q));
+        B::template dft<true>(a);
+#pragma unroll
+        for (int t = 0; t < R; ++t) xb[t * st] = a[B::slot(t)];
+    }
+    __syncthreads();
+}
+
+// Inverse stage 0 with the chirp in its stores: output n < N becomes conj^INV(y_n c_n).
+template <class B, bool INV>
+__device__ __forceinline__ void blue_last_stage(float2* __restrict__ x, int lgc,
+                                                const FftPlanDev& p, const float2* __restrict__ tw)
+{
+    constexpr int R = B::R;
+    const unsigned mask = (1u << lgc) - 1u;
+    const unsigned m = (unsigned)p.span[0];
+    const unsigned total = (unsigned)(p.L / R) << lgc;
+    const unsigned st = m << lgc;
+    const unsigned N = (unsigned)p.N;
+    for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
+        const unsigned col = b & mask;
+        const unsigned j = b >> lgc;
+        float2* xb = x + ((j << lgc) + col);
+        float2 w[R], v[R];
+        twiddle_powers<R, B::F>(w, tw, j);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 a = xb[q * st];
+            v[q] = q ? cmulc(a, w[q]) : a;
+        }
+        B::template dft<true>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const unsigned n = j + t * m;
+            if (n < N) {
+                const float2 o = cmul(v[B::slot(t)], __ldg(p.chirp + n));
+                xb[t * st] = INV ? cconj(o) : o;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Not inlined: one copy serves every driver (the runtime column shift), which keeps the nine
+// radices of its five stage kinds out of each kernel's compilation.
+template <bool INV>
+__device__ __noinline__ void bluestein_fused(float2* x, int lgc, const FftPlanDev& p,
+                                             const float2* tw)
+{
+    const int Lw = p.L, nl = p.nst - 1;
+    with_radix(p.radix[0], [&](auto bf) { blue_first_stage<decltype(bf), INV>(x, lgc, p, tw); });
+    for (int s = 1; s < nl; ++s) {
+        const int R = p.radix[s], m = p.span[s];
+        const unsigned mg = p.magic[s];
+        with_radix(R, [&](auto bf) {
+            dif_stage<decltype(bf), -1, false>(x, lgc, Lw, m, mg, Lw / (m * R), tw, 0, 0u);
+        });
+        __syncthreads();
+    }
+    with_radix(p.radix[nl], [&](auto bf) { blue_middle_stage<decltype(bf)>(x, lgc, p); });
+    for (int s = nl - 1; s >= 1; --s) {
+        const int R = p.radix[s], m = p.span[s];
+        const unsigned mg = p.magic[s];
+        with_radix(R, [&](auto bf) {
+            dit_inv_stage<decltype(bf), -1, false>(x, lgc, Lw, m, mg, Lw / (m * R), tw, 0, 0u);
+        });
+        __syncthreads();
+    }
+    with_radix(p.radix[0], [&](auto bf) { blue_last_stage<decltype(bf), INV>(x, lgc, p, tw); });
+}
+
 // Forward DFT of every column: natural input; frequency k ends at position perm[k].
 // LGC >= 0 fixes lgc at compile time (rows: 0); LGC = -1 reads it at run time.  PAD: x is a
 // padded row buffer (Bluestein plans have no padding).
@@ -488,8 +640,12 @@ template <int LGC = -1, bool PAD = false>
 __device__ __forceinline__ void fft_forward(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
-    if (p.bluestein) bluestein<false, LGC>(x, lgc, p, tw);
-    else direct_forward<LGC, PAD>(x, lgc, p, tw);
+    if (p.bluestein) {
+        if (p.nst >= 2) bluestein_fused<false>(x, LGC >= 0 ? LGC : lgc, p, tw);
+        else bluestein<false, LGC>(x, lgc, p, tw);
+    } else {
+        direct_forward<LGC, PAD>(x, lgc, p, tw);
+    }
 }
 
 // Unnormalised inverse DFT: frequency k read from position perm[k]; natural output.
@@ -497,8 +653,12 @@ template <int LGC = -1, bool PAD = false>
 __device__ __forceinline__ void fft_inverse(float2* x, int lgc, const FftPlanDev& p,
                                             const float2* tw)
 {
-    if (p.bluestein) bluestein<true, LGC>(x, lgc, p, tw);
-    else direct_inverse<LGC, PAD>(x, lgc, p, tw);
+    if (p.bluestein) {
+        if (p.nst >= 2) bluestein_fused<true>(x, LGC >= 0 ? LGC : lgc, p, tw);
+        else bluestein<true, LGC>(x, lgc, p, tw);
+    } else {
+        direct_inverse<LGC, PAD>(x, lgc, p, tw);
+    }
 }
 
 // Buffer index of work position q in a padded row buffer.
