@@ -175,8 +175,9 @@ int blfls_gaussian(blfls_handle *h, const float *img, float *out, int H, int W, 
  * call computes, with R from the FP32 gradients (a constant field, R = 0, keeps sigma_r).  The
  * result does not change when the image is scaled by any factor (scaled by it).  Arguments,
  * precisions, radii and errors as blfls_smooth; device pointers [C][H][W], out may equal img.
- * Each pass reads the fields' ranges back to the host, so the call synchronises `stream` once
- * per pass, and the channels run one after another. */
+ * The fields' ranges and the range constants derived from them are computed on the device, so
+ * the call is asynchronous on `stream` like blfls_smooth (no host synchronisation); the channels
+ * run one after another on `stream`. */
 int blfls_smooth_normalized(blfls_handle *h, const float *img, float *out, int H, int W, int C,
                             float lambda, float sigma_s, float sigma_r, int radius, int iters,
                             int prec, void *stream);

@@ -497,6 +497,7 @@ void blfls_destroy(blfls_handle* h)
     if (h->grid_a) cudaFree(h->grid_a);
     if (h->grid_keys) cudaFree(h->grid_keys);
     if (h->grid_keys_host) cudaFreeHost(h->grid_keys_host);
+    if (h->kap_dev) cudaFree(h->kap_dev);
     if (h->nc_scratch) cudaFree(h->nc_scratch);
     if (h->chan_scratch) cudaFree(h->chan_scratch);
     for (cudaStream_t st : h->chan_streams) cudaStreamDestroy(st);
@@ -859,6 +860,8 @@ static int ensure_range_keys(blfls_handle* h)
 {
     int rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "range keys");
     if (rc != BLFLS_OK) return rc;
+    rc = grow(h, h->kap_dev, h->kap_cap, (size_t)BLFLS_MAX_CHANNELS, "range constants");
+    if (rc != BLFLS_OK) return rc;
     if (!h->grid_keys_host) {
         void* p = nullptr;
         const cudaError_t e = cudaMallocHost(&p, sizeof(int) * 4 * BLFLS_MAX_CHANNELS);
@@ -895,25 +898,14 @@ int blfls_smooth_normalized(blfls_handle* h, const float* img, float* out, int H
     const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
-        // the ranges of both fields of every channel of this pass's input
+        // the ranges of both fields of every channel of this pass's input, and from them the
+        // range constants K1 reads, all on the device (no read-back)
         cudaError_t e = launch_grid_minmax(src, H, W, C, h->grid_keys, s, h->num_sms);
+        if (e == cudaSuccess) e = launch_range_kappa(h->grid_keys, C, sigma_r, h->kap_dev, s);
         if (e != cudaSuccess) return cuda_fail(e, "range kernel launch");
-        e = cudaMemcpyAsync(h->grid_keys_host, h->grid_keys, sizeof(int) * 4 * C,
-                            cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "range read-back");
         for (int c = 0; c < C; ++c) {
             BlfParams bp{H, W, radius, sigma_s, sigma_r, prec, tuned_tile_h(h, radius, prec)};
-            float scale[2];
-            for (int field = 0; field < 2; ++field) {
-                const int q = 2 * c + field;
-                const float lo = grid_key_to_float(h->grid_keys_host[2 * q]);
-                const float hi = grid_key_to_float(h->grid_keys_host[2 * q + 1]);
-                const float range = hi - lo;
-                scale[field] = range > 0.f ? range : 1.0f;   // a constant field is unchanged
-            }
-            bp.range_scale_x = scale[0];
-            bp.range_scale_y = scale[1];
+            bp.kap_dev = h->kap_dev + c;
             const float* fc = src + c * plane;
             e = blf_launch(h, fc, h->ex, h->ey, 1, bp, s);
             if (e != cudaSuccess) return cuda_fail(e, "bilateral kernel launch");

@@ -46,10 +46,12 @@ template <bool RANGE>
 __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __restrict__ img,
                                                                float* __restrict__ ex,
                                                                float* __restrict__ ey, int H,
-                                                               int W, int R, int th, const Kap k,
-                                                               float cs)
+                                                               int W, int R, int th, const Kap k0,
+                                                               float cs,
+                                                               const float4* __restrict__ kdev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const Kap k = kap_of(k0, kdev, blockIdx.z);
     const int fp = f_pitch(R), gp = g_pitch(R), gr = g_rows(R, th);
     float* sf = reinterpret_cast<float*>(smem);
     float* gx = reinterpret_cast<float*>(smem + f_bytes(R, th));
@@ -101,9 +103,14 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __re
 }
 
 // Radii above the tiled limit: gradients precomputed to global memory, one pixel per thread.
+// kdev (when set) holds this channel's range constants (kx, ky, 1/kx, 1/ky).
 __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ g, int H, int W,
-                             float kx, float ky)
+                             float kx, float ky, const float4* __restrict__ kdev)
 {
+    if (kdev) {
+        kx = kdev->x;
+        ky = kdev->y;
+    }
     const size_t plane = (size_t)H * W;
     float* gx = g;
     float* gy = g + plane;
@@ -121,8 +128,12 @@ __global__ void k1_gradients(const float* __restrict__ img, float* __restrict__ 
 template <bool RANGE>
 __global__ void k1_blf_global(const float* __restrict__ g, const float* __restrict__ hg,
                               float* __restrict__ ex, float* __restrict__ ey, int H, int W, int R,
-                              float inv_kx, float inv_ky, float cs)
+                              float inv_kx, float inv_ky, float cs, const float4* __restrict__ kdev)
 {
+    if (kdev) {
+        inv_kx = kdev->z;
+        inv_ky = kdev->w;
+    }
     const size_t plane = (size_t)H * W;
     const float* gx = g;
     const float* gy = g + plane;
@@ -231,14 +242,14 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
         } else if (R <= kMaxTemplR) {
             TiledFn fn = pick_tiled_prec(p.prec, R, range);
             fn<<<grid, threads, blf_templ_smem_bytes(R, p.prec, th), s>>>(img, ex, ey, p.H, p.W, th,
-                                                                         k, cs);
+                                                                         k, cs, p.kap_dev);
         } else {
             if (p.prec != 0) return cudaErrorNotSupported;
             const size_t smem = tile_smem_bytes(R, sizeof(float), th);
             if (range)
-                k1_blf_tiled_rt<true><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs);
+                k1_blf_tiled_rt<true><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs, p.kap_dev);
             else
-                k1_blf_tiled_rt<false><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs);
+                k1_blf_tiled_rt<false><<<grid, threads, smem, s>>>(img, ex, ey, p.H, p.W, R, th, k, cs, p.kap_dev);
         }
         return cudaGetLastError();
     }
@@ -248,12 +259,13 @@ cudaError_t launch_blf_residual(const float* img, float* ex, float* ey, int C, c
     const int blocks = (int)std::min<size_t>((plane + 255) / 256, 4096);
     float* hg = joint ? gscratch + 2 * plane : nullptr;
     for (int c = 0; c < C; ++c) {
-        k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kx, ky);
-        if (joint) k1_gradients<<<blocks, 256, 0, s>>>(p.guide + c * p.guide_stride, hg, p.H, p.W, kx, ky);
+        const float4* kd = p.kap_dev ? p.kap_dev + c : nullptr;
+        k1_gradients<<<blocks, 256, 0, s>>>(img + c * plane, gscratch, p.H, p.W, kx, ky, kd);
+        if (joint) k1_gradients<<<blocks, 256, 0, s>>>(p.guide + c * p.guide_stride, hg, p.H, p.W, kx, ky, kd);
         if (range)
-            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, hg, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs);
+            k1_blf_global<true><<<blocks, 256, 0, s>>>(gscratch, hg, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs, kd);
         else
-            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, nullptr, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs);
+            k1_blf_global<false><<<blocks, 256, 0, s>>>(gscratch, nullptr, ex + c * plane, ey + c * plane, p.H, p.W, R, ikx, iky, cs, kd);
     }
     return cudaGetLastError();
 }

@@ -406,18 +406,27 @@ __device__ __forceinline__ void blf_tile(const float* f, const float* guide, flo
     else tile_f32<R, RANGE, JOINT>(f, guide, ex, ey, H, W, x0, y0, th, k, cs, smem);
 }
 
+// The range constants of channel z: from the device when kdev is set, else the launch's.
+__device__ __forceinline__ Kap kap_of(const Kap k, const float4* __restrict__ kdev, int z)
+{
+    if (!kdev) return k;
+    const float4 v = kdev[z];
+    return Kap{v.x, v.y, v.z, v.w};
+}
+
 // One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.
 template <int R, bool RANGE, int PREC>
 __global__ void __launch_bounds__(kMaxThreads) k1_blf(const float* __restrict__ img,
                                                       float* __restrict__ ex,
                                                       float* __restrict__ ey, int H, int W,
-                                                      int th, const Kap k, float cs)
+                                                      int th, const Kap k, float cs,
+                                                      const float4* __restrict__ kdev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t plane = (size_t)H * W;
     blf_tile<R, RANGE, PREC>(img + blockIdx.z * plane, nullptr, ex + blockIdx.z * plane,
                              ey + blockIdx.z * plane, H, W, blockIdx.x * kTW, blockIdx.y * th,
-                             th, k, cs, smem);
+                             th, kap_of(k, kdev, blockIdx.z), cs, smem);
 }
 
 // Joint form: as k1_blf with the range kernel on, guided by channel z of `guide` (channel
@@ -463,7 +472,8 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_batch(const BatchJob* __re
 
 }  // namespace
 
-using TiledFn = void (*)(const float*, float*, float*, int, int, int, const Kap, float);
+using TiledFn = void (*)(const float*, float*, float*, int, int, int, const Kap, float,
+                         const float4*);
 using BatchFn = void (*)(const BatchJob*, const int2*, int, int);
 using JointFn = void (*)(const float*, const float*, size_t, float*, float*, int, int, int,
                          const Kap, float);

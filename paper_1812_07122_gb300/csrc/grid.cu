@@ -176,6 +176,34 @@ __global__ void __launch_bounds__(kGridThreads) k6_slice(const float* __restrict
     }
 }
 
+__device__ __forceinline__ float key_to_float(int key)
+{
+    return __int_as_float(key ^ ((key >> 31) & 0x7fffffff));
+}
+
+// Range constants of every channel for normalised gradients: each field's range R = max - min
+// (1 for a constant field), sigma_r R in FP32, then kappa = sqrt(log2(e) / (2 (sigma_r R)^2)) and
+// 1 / kappa in FP64 rounded to FP32 -- the host's blf_constants, operation for operation.
+__global__ void k6_range_kappa(const int* __restrict__ keys, int C, float sigma_r,
+                               float4* __restrict__ kap)
+{
+    const int c = threadIdx.x;
+    if (c >= C) return;
+    float k[2], ik[2];
+#pragma unroll
+    for (int fl = 0; fl < 2; ++fl) {
+        const float lo = key_to_float(keys[4 * c + 2 * fl]);
+        const float hi = key_to_float(keys[4 * c + 2 * fl + 1]);
+        const float range = hi - lo;
+        const float sr = sigma_r * (range > 0.f ? range : 1.0f);
+        double kd = 1.0;
+        if (isfinite(sr)) kd = sqrt(1.4426950408889634 / (2.0 * (double)sr * sr));
+        k[fl] = (float)kd;
+        ik[fl] = (float)(1.0 / kd);
+    }
+    kap[c] = make_float4(k[0], k[1], ik[0], ik[1]);
+}
+
 int stream_blocks(size_t n, int num_sms)
 {
     const size_t want = (n + kGridThreads - 1) / kGridThreads;
@@ -190,6 +218,12 @@ cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys,
     k6_init_keys<<<1, 32, 0, s>>>(keys, 4 * C);
     dim3 grid(stream_blocks((size_t)H * W, num_sms) / std::max(1, C) + 1, C);
     k6_minmax<<<grid, kGridThreads, 0, s>>>(img, H, W, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_range_kappa(const int* keys, int C, float sigma_r, float4* kap, cudaStream_t s)
+{
+    k6_range_kappa<<<1, 32, 0, s>>>(keys, C, sigma_r, kap);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ struct blfls_handle {
     int* grid_keys = nullptr;
     size_t grid_keys_cap = 0;
     int* grid_keys_host = nullptr;   // pinned, 4 * BLFLS_MAX_CHANNELS
+    float4* kap_dev = nullptr;       // blfls_smooth_normalized: range constants per channel
+    size_t kap_cap = 0;
     float* nc_scratch = nullptr;     // blfls_smooth_nc: gradients, transforms, two buffers
     size_t nc_cap = 0;
     // blfls_smooth: channels 1..C-1 run on their own streams with their own residual planes and

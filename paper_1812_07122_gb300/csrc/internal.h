@@ -106,6 +106,10 @@ struct BlfParams {
     // Range widths per field: field x uses sigma_r * range_scale_x, field y sigma_r *
     // range_scale_y (1 and 1 unless each field is normalised to its own range).
     float range_scale_x = 1.0f, range_scale_y = 1.0f;
+    // When set, the range constants (kx, ky, 1/kx, 1/ky) of channel c are read from the device at
+    // kap_dev[c] instead (computed there from the fields' ranges, see launch_range_kappa), so the
+    // host need not wait for the ranges.
+    const float4* kap_dev = nullptr;
 };
 
 // Launch K1 over channels [0, C) of img (planes of H*W floats).  `gscratch` must hold
@@ -178,6 +182,9 @@ cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int 
 cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys, cudaStream_t s,
                                int num_sms);
 float grid_key_to_float(int key);
+// Normalised gradients: per channel, the range constants (kx, ky, 1/kx, 1/ky) of the two fields
+// from their range keys (launch_grid_minmax), sigma_r scaled by each field's range, on the device.
+cudaError_t launch_range_kappa(const int* keys, int C, float sigma_r, float4* kap, cudaStream_t s);
 void grid_dims(int H, int W, float lo, float hi, float sigma_s, float sigma_r, int* gx, int* gy,
                int* gz);
 cudaError_t launch_grid_residual(const float* f, float* e, int field, int H, int W, float sigma_s,

@@ -80,3 +80,23 @@ def test_normalized_in_place_zero_iters_and_rejects_bad_arguments(h):
             blfls.blfls_smooth_normalized(h, x, out, 40, 48, 2, lam, ss, sr, r, iters, prec,
                                           stream())
         assert ei.value.code == blfls.BLFLS_EINVAL
+
+
+def test_normalized_call_does_not_wait_for_the_gpu(h):
+    """The fields' ranges and range constants are computed on the device: with the stream held
+    busy by a bounded spin, the call returns while the stream is still busy, and its result is
+    the same as the same call made on an idle stream."""
+    f = _img(96, 128, 3, seed=21)
+    want = _norm(h, f, 20.0, 3.0, 0.1, 4, iters=2)       # also builds plans and scratch
+    x = to_dev(f)
+    out = torch.empty_like(x)
+    torch.cuda.synchronize(DEV)
+    s = stream()
+    torch.cuda._sleep(200_000_000)                        # ~0.1 s of spinning on the stream
+    blfls.blfls_smooth_normalized(h, x, out, 96, 128, 3, 20.0, 3.0, 0.1, 4, 2,
+                                  blfls.BLFLS_FP32, s)
+    done = torch.cuda.Event()
+    done.record(s)
+    assert not done.query(), "the call waited for the stream"
+    torch.cuda.synchronize(DEV)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
