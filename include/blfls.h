@@ -359,6 +359,19 @@ int blfls_autotune(blfls_handle *h, int H, int W, int C, int radius, int prec,
  * memory.  Returns BLFLS_EINVAL for a bad device or rates == NULL. */
 int blfls_pipe_rates(int device, double *rates, int n);
 
+/* Device-side range checks (no counterpart in the paper; a stand-in for a memory checker).  A
+ * library compiled with -DBLFLS_DEVICE_CHECKS (paper_1812_07122_gb300/build.py, debug=True)
+ * checks the index arithmetic of its kernels at run time -- image tile loads and window reads
+ * of the bilateral kernels, every FFT butterfly's buffer offsets, the solve drivers' global
+ * indices, grid cells, NC tile indices -- and, instead of performing an access that would leave
+ * its buffer, sets one bit per kind of check in a device word and skips it (no trap, no assert,
+ * no wait).  This call waits for `device` to finish its work, then writes the OR of those words
+ * since the last call to *word (bits: 0 tile load, 1 window read, 2 residual store, 3 FFT
+ * stage, 4 solve global index, 5 grid cell, 6 NC tile) and clears them.  In a release build the
+ * checks compile away and *word is always 0.  Errors: BLFLS_EINVAL (word NULL, bad device),
+ * BLFLS_ECUDA. */
+int blfls_device_checks(int device, unsigned int *word);
+
 /* Step 2 without any device allocation (the paper has no counterpart; this is a deployment
  * variant of blfls_solve_residual).
  *

@@ -13,6 +13,9 @@ import ctypes
 import os
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libblfls.so")
+# BLFLS_LIBRARY names another build of the same library to load instead (for example the debug
+# build with device range checks, see build.py); it must exist like the default one.
+LIB_ENV = "BLFLS_LIBRARY"
 
 BLFLS_OK = 0
 BLFLS_EINVAL = -1
@@ -104,6 +107,7 @@ _SIGNATURES = {
     "blfls_server_get_stats": (_c_int, [_vp, ctypes.POINTER(blfls_server_stats)]),
     "blfls_autotune": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.c_char_p]),
     "blfls_pipe_rates": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double), _c_int]),
+    "blfls_device_checks": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_uint)]),
     "blfls_solve_residual_noalloc": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int,
                                               _c_float, _vp]),
     "blfls_profile_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
@@ -128,10 +132,11 @@ def load():
     """Load the library (once).  Raises if it has not been built."""
     global _LIB
     if _LIB is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+        path = os.environ.get(LIB_ENV) or LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
                                "`python -m paper_1812_07122_gb300.build` (needs nvcc)")
-        lib = ctypes.CDLL(LIB_PATH)
+        lib = ctypes.CDLL(path)
         for name, (res, args) in _SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -426,3 +431,10 @@ class Smoother:
         blfls_smooth(self.h, img, out, H, W, C, lam, sigma_s, sigma_r, radius, iters, prec,
                      stream)
         return out
+
+
+def blfls_device_checks(device: int = 0) -> int:
+    """OR of the device range-check words since the last call (0 in a release build)."""
+    w = ctypes.c_uint()
+    _check(load().blfls_device_checks(int(device), ctypes.byref(w)))
+    return int(w.value)

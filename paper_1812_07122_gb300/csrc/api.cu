@@ -444,7 +444,36 @@ constexpr size_t kSubmitDefaultBudget = (size_t)8 << 30;
 constexpr int kSubmitSlots = 2;
 constexpr int kSubmitMaxBatch = 64;
 
+namespace blfls {
+// The check words of the translation units with device range checks (dcheck.cuh).
+unsigned int dcheck_fetch_blf_f32();
+unsigned int dcheck_fetch_blf_f16();
+unsigned int dcheck_fetch_blf_bf16();
+unsigned int dcheck_fetch_blf_kernels();
+unsigned int dcheck_fetch_solve_kernels();
+unsigned int dcheck_fetch_grid();
+unsigned int dcheck_fetch_nc();
+}  // namespace blfls
+
 extern "C" {
+
+int blfls_device_checks(int device, unsigned int* word)
+{
+    if (!word) return fail(BLFLS_EINVAL, "word is NULL");
+    *word = 0;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(BLFLS_EINVAL, "no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(BLFLS_ECUDA, "cudaSetDevice failed");
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    *word = dcheck_fetch_blf_f32() | dcheck_fetch_blf_f16() | dcheck_fetch_blf_bf16() |
+            dcheck_fetch_blf_kernels() | dcheck_fetch_solve_kernels() | dcheck_fetch_grid() |
+            dcheck_fetch_nc();
+    return BLFLS_OK;
+}
 
 int blfls_create(blfls_handle** out, int device, size_t mem_budget_bytes,
                  const char* tune_table_path)

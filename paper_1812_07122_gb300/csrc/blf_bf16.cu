@@ -40,6 +40,8 @@ JointFn pick_joint_bf16(int r)
 
 }  // namespace
 
+BLFLS_DCHECK_TU(blf_bf16)
+
 JointFn pick_joint_bf16_entry(int r) { return pick_joint_bf16<0>(r); }
 TiledFn pick_tiled_bf16_entry(int r, bool range) { return pick_tiled_bf16<0>(r, range); }
 BatchFn pick_batch_bf16_entry(int r, bool range) { return pick_batch_bf16<0>(r, range); }

@@ -40,6 +40,8 @@ JointFn pick_joint_f16(int r)
 
 }  // namespace
 
+BLFLS_DCHECK_TU(blf_f16)
+
 JointFn pick_joint_f16_entry(int r) { return pick_joint_f16<0>(r); }
 TiledFn pick_tiled_f16_entry(int r, bool range) { return pick_tiled_f16<0>(r, range); }
 BatchFn pick_batch_f16_entry(int r, bool range) { return pick_batch_f16<0>(r, range); }

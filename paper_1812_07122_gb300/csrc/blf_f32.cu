@@ -40,6 +40,8 @@ JointFn pick_joint_f32(int r)
 
 }  // namespace
 
+BLFLS_DCHECK_TU(blf_f32)
+
 JointFn pick_joint_f32_entry(int r) { return pick_joint_f32<0>(r); }
 TiledFn pick_tiled_f32_entry(int r, bool range) { return pick_tiled_f32<0>(r, range); }
 BatchFn pick_batch_f32_entry(int r, bool range) { return pick_batch_f32<0>(r, range); }

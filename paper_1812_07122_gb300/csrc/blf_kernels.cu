@@ -16,6 +16,8 @@ JointFn pick_joint_f32_entry(int r);
 JointFn pick_joint_f16_entry(int r);
 JointFn pick_joint_bf16_entry(int r);
 
+BLFLS_DCHECK_TU(blf_kernels)
+
 JointFn pick_joint_prec(int prec, int r)
 {
     if (prec == 1) return pick_joint_f16_entry(r);
@@ -77,6 +79,10 @@ __global__ void __launch_bounds__(kMaxThreads) k1_blf_tiled_rt(const float* __re
     }
     for (int dy = -R; dy <= R; ++dy) {
         for (int dx = -R; dx <= R; ++dx) {
+            if (!BLFLS_DCHECK(R + cx + dx >= 0 && R + cx + dx < gp && r0 + dy + R >= 0 &&
+                              (R + r0 + dy + kStrip - 1) * gp + R + cx + dx < gr * gp,
+                              kDcTileWindow))
+                continue;
             const float a = -float(dx * dx + dy * dy) * cs;
             const float* px = gx + (R + r0 + dy) * gp + R + cx + dx;
             const float* py = gy + (R + r0 + dy) * gp + R + cx + dx;

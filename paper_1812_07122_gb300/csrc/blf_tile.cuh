@@ -24,6 +24,7 @@
 // kMaxTiledR use a scalar FP32 kernel with a runtime window; above that a per-pixel kernel reads
 // precomputed gradients from global memory.
 #pragma once
+#include "dcheck.cuh"
 #include "internal.h"
 
 #include <cmath>
@@ -134,12 +135,15 @@ __device__ __forceinline__ void load_f_tile(const float* __restrict__ f, int H, 
 #pragma unroll
     for (int k = 0; k < kTileColsPerLane; ++k) xs[k] = wrap_idx(x0 - R + lane + 32 * k, W);
     for (int r = threadIdx.x >> 5; r < fr; r += nw) {
-        const float* row = f + (size_t)wrap_idx(y0 - R + r, H) * W;
+        const int yy = wrap_idx(y0 - R + r, H);
+        if (!BLFLS_DCHECK(yy >= 0 && yy < H, kDcTileLoad)) continue;
+        const float* row = f + (size_t)yy * W;
         float* srow = sf + r * fp;
 #pragma unroll
         for (int k = 0; k < kTileColsPerLane; ++k) {
             const int c = lane + 32 * k;
-            if (c < fp) srow[c] = __ldg(row + xs[k]);
+            if (c < fp && BLFLS_DCHECK(xs[k] >= 0 && xs[k] < W, kDcTileLoad))
+                srow[c] = __ldg(row + xs[k]);
         }
     }
 }
@@ -160,7 +164,7 @@ __device__ __forceinline__ void store_strip(float* __restrict__ ex, float* __res
                                             const float* zx, const float* sx, const float* ay,
                                             const float* zy, const float* sy, const Kap k)
 {
-    if (x >= W) return;
+    if (x >= W || !BLFLS_DCHECK(x >= 0 && ybase >= 0, kDcTileStore)) return;
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
         const int y = ybase + j;
@@ -234,6 +238,10 @@ __device__ __forceinline__ void tile_pair_fields(const float* __restrict__ f,
 
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
+        // this column's reads: rows r0 .. r0 + kStrip + 2R - 1 of tile column R + cx + dx
+        if (!BLFLS_DCHECK(R + cx + dx >= 0 && R + cx + dx < gp &&
+                          (r0 + kStrip + 2 * R - 1) * gp + R + cx + dx < gr * gp, kDcTileWindow))
+            continue;
         const float gdx = ex2_approx(-float(dx * dx) * cs);     // the dx part of the weight
         const u64 GD = pk(gdx, gdx);
         const u64* col = reinterpret_cast<const u64*>(g + r0 * gp + R + cx + dx);
@@ -352,6 +360,9 @@ __device__ __forceinline__ void tile_f16(const float* __restrict__ f, const floa
 
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
+        if (!BLFLS_DCHECK(R + cx + dx >= 0 && R + cx + dx < gp &&
+                          (r0 + kStrip + 2 * R - 1) * gp + R + cx + dx < gr * gp, kDcTileWindow))
+            continue;
         const float gdx = ex2_approx(-float(dx * dx) * cs);
         const u64 GD = pk(gdx, gdx);
         __half2 P[kStrip], Q[kStrip];    // this column's sums of w t and w

@@ -16,6 +16,7 @@
 // transforms; input and output are in natural order, positions [N, L) are scratch.
 #pragma once
 
+#include "dcheck.cuh"
 #include "internal.h"
 
 #include <type_traits>
@@ -326,6 +327,7 @@ __device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, in
     const unsigned um = (unsigned)m, lblk = um * R;
     const bool twiddled = m > 1;
     const bool pad = PAD && pad_span > 0;
+    const unsigned limit = ((unsigned)Lw << lgc) + (pad ? (unsigned)(Lw / pad_span) : 0u);
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> lgc;
@@ -337,6 +339,7 @@ __device__ __forceinline__ void dif_stage(float2* __restrict__ x, int lgc_rt, in
             base += __umulhi(base, pad_magic);
             if (um == (unsigned)pad_span) st = um + 1;
         }
+        if (!BLFLS_DCHECK((base << lgc) + col + (R - 1) * st < limit, kDcFftStage)) continue;
         float2* xb = x + ((base << lgc) + col);
         float2 v[R];
 #pragma unroll
@@ -371,6 +374,7 @@ __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt
     const unsigned um = (unsigned)m, lblk = um * R;
     const bool twiddled = m > 1;
     const bool pad = PAD && pad_span > 0;
+    const unsigned limit = ((unsigned)Lw << lgc) + (pad ? (unsigned)(Lw / pad_span) : 0u);
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> lgc;
@@ -382,6 +386,7 @@ __device__ __forceinline__ void dit_inv_stage(float2* __restrict__ x, int lgc_rt
             base += __umulhi(base, pad_magic);
             if (um == (unsigned)pad_span) st = um + 1;
         }
+        if (!BLFLS_DCHECK((base << lgc) + col + (R - 1) * st < limit, kDcFftStage)) continue;
         float2* xb = x + ((base << lgc) + col);
         float2 v[R];
         if (twiddled) {
@@ -519,6 +524,8 @@ __device__ __forceinline__ void blue_first_stage(float2* __restrict__ x, int lgc
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned j = b >> lgc;                       // stage 0: one block, base = j
+        if (!BLFLS_DCHECK(((j + (R - 1) * m) << lgc) + col < ((unsigned)p.L << lgc), kDcFftStage))
+            continue;
         float2* xb = x + ((j << lgc) + col);
         float2 v[R];
 #pragma unroll
@@ -556,6 +563,8 @@ __device__ __forceinline__ void blue_middle_stage(float2* __restrict__ x, int lg
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned base = (b >> lgc) * R;
+        if (!BLFLS_DCHECK(((base + R - 1) << lgc) + col < ((unsigned)p.L << lgc), kDcFftStage))
+            continue;
         float2* xb = x + ((base << lgc) + col);
         float2 v[R], a[R];
 #pragma unroll
@@ -584,6 +593,8 @@ __device__ __forceinline__ void blue_last_stage(float2* __restrict__ x, int lgc,
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned j = b >> lgc;
+        if (!BLFLS_DCHECK(((j + (R - 1) * m) << lgc) + col < ((unsigned)p.L << lgc), kDcFftStage))
+            continue;
         float2* xb = x + ((j << lgc) + col);
         float2 w[R], v[R];
         twiddle_powers<R, B::F>(w, tw, j);
@@ -702,6 +713,7 @@ __device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* _
     constexpr unsigned lblk = (unsigned)M * R;
     constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : ((unsigned)M << LGC);
     constexpr unsigned tw_step = (unsigned)(L / (M * R));
+    constexpr unsigned limit = ((unsigned)L << LGC) + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
         const unsigned col = b & mask;
         const unsigned bi = b >> LGC;
@@ -709,6 +721,7 @@ __device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* _
         const unsigned j = bi - blk * (unsigned)M;
         unsigned base = blk * lblk + j;
         if constexpr (PADS > 0) base += base / (unsigned)PADS;
+        if (!BLFLS_DCHECK((base << LGC) + col + (R - 1) * st < limit, kDcFftStage)) continue;
         float2* xb = x + ((base << LGC) + col);
         float2 v[R];
         if constexpr (!INV) {
@@ -775,6 +788,12 @@ struct CtStage {
         unsigned base = nat;
         if constexpr (PADS > 0) base += base / (unsigned)PADS;
         return (base << LGC) + col;
+    }
+    // the butterfly at buffer offset off stays inside the transform buffer
+    static __device__ __forceinline__ bool in_buffer(unsigned off)
+    {
+        constexpr unsigned limit = ((unsigned)L << LGC) + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
+        return BLFLS_DCHECK(off + (R - 1) * st < limit, kDcFftStage);
     }
     // forward (decimation in frequency): v in input order t -> out[q] = DFT(v)_q w^(j q)
     static __device__ __forceinline__ void fwd(float2 (&v)[R], float2 (&out)[R],

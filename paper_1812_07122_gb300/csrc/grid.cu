@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dcheck.cuh"
 #include "internal.h"
 
 namespace blfls {
@@ -117,6 +118,9 @@ __global__ void __launch_bounds__(kGridThreads) k6_splat(const float* __restrict
                 if (cell_of((float)x, 0.0f, G.ss) != kx) continue;
                 const float g = grad_at(f, G.H, G.W, y, x, G.field);
                 const int z = cell_of(g, G.lo, G.sr) + kPad;
+                if (!BLFLS_DCHECK(z >= 0 && z < G.gz && ky + kPad < G.gy && kx + kPad < G.gx,
+                                  kDcGridCell))
+                    continue;
                 float2* c = col + (size_t)z * slab;
                 c->x += g;
                 c->y += 1.f;
@@ -211,6 +215,8 @@ int stream_blocks(size_t n, int num_sms)
 }
 
 }  // namespace
+
+BLFLS_DCHECK_TU(grid)
 
 cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys, cudaStream_t s,
                                int num_sms)

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dcheck.cuh"
 #include "internal.h"
 
 namespace blfls {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kNcThreads) k8_nc_rows_tile(const float* __res
         if (y >= H) break;
         for (int q = lane; q < kTileLong; q += 32) {
             const int x = x0 + q;
-            if (x < W)
+            if (x < W && BLFLS_DCHECK(q + 2 * R < span, kDcNcTile))
                 out[(size_t)y * W + x] = tile_mean(ss + r * span, sv + r * span, 1, R + q, R,
                                                    (unsigned long long)rq);
         }
@@ -423,6 +424,8 @@ void nc_box_pass(const float* v, const unsigned* sh, float* mid, const unsigned*
 }
 
 }  // namespace
+
+BLFLS_DCHECK_TU(nc)
 
 cudaError_t launch_nc_residuals(const float* f, float* ex, float* ey, int H, int W,
                                 float sigma_s, float sigma_r, int n_iter, float* scratch,

@@ -187,7 +187,8 @@ __device__ __forceinline__ void k3_item(float2* __restrict__ spec, int H, int W,
     for (int i = threadIdx.x; i < (H << lgc); i += blockDim.x) {
         const int n = i >> lgc, c = i & (CB - 1);
         const int kx = kx0 + c;
-        data[i] = (kx < Wh) ? spec[(size_t)n * Wh + kx] : make_float2(0.f, 0.f);
+        data[i] = (kx < Wh && BLFLS_DCHECK(n < H && kx >= 0, kDcSolveGlobal))
+                      ? spec[(size_t)n * Wh + kx] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     k3_solve_block(data, H, W, kx0, lgc, cp, sx, sy, lam, scale, tw);
@@ -587,6 +588,9 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
         for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
+            if (!S0::in_buffer(S0::offset(nat, col)) ||
+                !BLFLS_DCHECK(nat + (R0 - 1) * M0 < (unsigned)W, kDcSolveGlobal))
+                continue;
             float2 v[R0];
 #pragma unroll
             for (int t = 0; t < R0; ++t) {
@@ -649,6 +653,9 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
             const int kx = kx0 + (int)col;
+            if (!S0::in_buffer(S0::offset(nat, col)) ||
+                !BLFLS_DCHECK(nat + (R0 - 1) * M0 < (unsigned)H, kDcSolveGlobal))
+                continue;
             float2 v[R0];
 #pragma unroll
             for (int t = 0; t < R0; ++t)
@@ -666,6 +673,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
         for (unsigned b = threadIdx.x; b < SL::total; b += blockDim.x) {
             unsigned nat, j, col;
             SL::locate(b, nat, j, col);
+            if (!SL::in_buffer(SL::offset(nat, col))) continue;
             float2* xb = data + SL::offset(nat, col);
             float2 v[RL], y[RL], o[RL];
 #pragma unroll
@@ -690,6 +698,9 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
             const int kx = kx0 + (int)col;
+            if (!S0::in_buffer(S0::offset(nat, col)) ||
+                !BLFLS_DCHECK(nat + (R0 - 1) * M0 < (unsigned)H, kDcSolveGlobal))
+                continue;
             const float2* xb = data + S0::offset(nat, col);
             float2 a[R0], o[R0];
 #pragma unroll
@@ -757,6 +768,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2*
             const unsigned b = (i % (unsigned)R0) * (SL::total / (unsigned)R0) + i / (unsigned)R0;
             unsigned nat, j, col;
             SL::locate(b, nat, j, col);
+            if (!SL::in_buffer(SL::offset(nat, col))) continue;
             float2 v[RL], o[RL];
 #pragma unroll
             for (int q = 0; q < RL; ++q) {
@@ -786,6 +798,9 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2*
         for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
+            if (!S0::in_buffer(S0::offset(nat, col)) ||
+                !BLFLS_DCHECK(nat + (R0 - 1) * M0 < (unsigned)W, kDcSolveGlobal))
+                continue;
             const float2* xb = data + S0::offset(nat, col);
             float2 a[R0], z[R0];
 #pragma unroll
@@ -1010,6 +1025,8 @@ int threads_for(int work)
 }
 
 }  // namespace
+
+BLFLS_DCHECK_TU(solve_kernels)
 
 static void set_staged_attributes();   // below, with the plan pickers
 

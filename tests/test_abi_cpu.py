@@ -93,3 +93,7 @@ def test_every_entry_point_rejects_a_null_handle_on_the_host(lib, name, args):
     """Argument checks run on the host before anything touches the GPU: a NULL handle is
     BLFLS_EINVAL from every entry point that takes one."""
     assert getattr(lib, name)(None, *args) == blfls.BLFLS_EINVAL
+
+
+def test_device_checks_reject_a_null_word_on_the_host(lib):
+    assert lib.blfls_device_checks(0, None) == blfls.BLFLS_EINVAL
