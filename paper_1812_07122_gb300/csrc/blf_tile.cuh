@@ -425,9 +425,10 @@ __device__ __forceinline__ Kap kap_of(const Kap k, const float4* __restrict__ kd
     return Kap{v.x, v.y, v.z, v.w};
 }
 
-// One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.
+// One CTA per 32 x th tile (4 th threads); blockIdx.z selects the channel.  The FP32 and BF16W
+// forms are held to 64 registers so that four 256-thread CTAs fit on an SM; FP16W to 128 (two).
 template <int R, bool RANGE, int PREC>
-__global__ void __launch_bounds__(kMaxThreads) k1_blf(const float* __restrict__ img,
+__global__ void __launch_bounds__(kMaxThreads, PREC == 1 ? 2 : 4) k1_blf(const float* __restrict__ img,
                                                       float* __restrict__ ex,
                                                       float* __restrict__ ey, int H, int W,
                                                       int th, const Kap k, float cs,
