@@ -185,7 +185,8 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
             if ((rc = get_plan(h, j.W, &I.rp)) != BLFLS_OK) return rc;
             if ((rc = get_plan(h, j.H, &I.cp)) != BLFLS_OK) return rc;
             blf_constants(j.sigma_s, j.sigma_r, &I.kappa, &I.inv_kappa, &I.cs);
-            I.lgc = solve_fit_lgc(I.cp->L, tuned_col_block(h, I.cp->L));
+            const int tuned = tuned_col_block(h, I.cp->L);
+            I.lgc = solve_fit_lgc(I.cp->L, tuned > 0 ? tuned : h->col_block);
             // The batched column kernel takes the largest block of the batch as its shared
             // memory, so cap every job's block at kBatchColBytes: one long (e.g. Bluestein)
             // column set must not cut the occupancy of every other job's items.

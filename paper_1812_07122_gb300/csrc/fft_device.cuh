@@ -702,27 +702,27 @@ template <int R> struct Bfly { using type = OneLevel<R>; };
 template <> struct Bfly<15> { using type = TwoLevel<3, 5>; };
 template <> struct Bfly<9> { using type = TwoLevel<3, 3>; };
 
-// One stage of a compile-time plan of length L: radix R, span M, column shift LGC, row padding
-// span PADS (0: none); INV selects the inverse (dit_inv_stage) form.
-template <int R, int M, int L, int LGC, int PADS, bool INV>
+// One stage of a compile-time plan of length L: radix R, span M, NC interleaved columns
+// (element n of column c at n NC + c; NC = 1 for a row), row padding span PADS (0: none); INV
+// selects the inverse (dit_inv_stage) form.
+template <int R, int M, int L, int NC, int PADS, bool INV>
 __device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* __restrict__ tw)
 {
     using B = typename Bfly<R>::type;
-    constexpr unsigned total = (unsigned)(L / R) << LGC;
-    constexpr unsigned mask = (1u << LGC) - 1u;
+    constexpr unsigned total = (unsigned)(L / R) * NC;
     constexpr unsigned lblk = (unsigned)M * R;
-    constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : ((unsigned)M << LGC);
+    constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : (unsigned)M * NC;
     constexpr unsigned tw_step = (unsigned)(L / (M * R));
-    constexpr unsigned limit = ((unsigned)L << LGC) + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
+    constexpr unsigned limit = (unsigned)L * NC + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
     for (unsigned b = threadIdx.x; b < total; b += blockDim.x) {
-        const unsigned col = b & mask;
-        const unsigned bi = b >> LGC;
+        const unsigned col = b % (unsigned)NC;
+        const unsigned bi = b / (unsigned)NC;
         const unsigned blk = bi / (unsigned)M;
         const unsigned j = bi - blk * (unsigned)M;
         unsigned base = blk * lblk + j;
         if constexpr (PADS > 0) base += base / (unsigned)PADS;
-        if (!BLFLS_DCHECK((base << LGC) + col + (R - 1) * st < limit, kDcFftStage)) continue;
-        float2* xb = x + ((base << LGC) + col);
+        if (!BLFLS_DCHECK(base * NC + col + (R - 1) * st < limit, kDcFftStage)) continue;
+        float2* xb = x + (base * NC + col);
         float2 v[R];
         if constexpr (!INV) {
 #pragma unroll
@@ -764,21 +764,20 @@ __device__ __forceinline__ void ct_stage(float2* __restrict__ x, const float2* _
 // Butterfly geometry of stage (R, M) of a compile-time plan, for drivers that move a
 // butterfly's data between global memory, staging buffers and registers themselves (the first
 // and last stages of a transform) instead of through ct_stage.  Butterfly b covers column
-// `col` (b mod 2^LGC) and the natural positions nat + t M, t = 0..R-1; its elements sit at buffer
+// `col` (b mod NC) and the natural positions nat + t M, t = 0..R-1; its elements sit at buffer
 // offsets off + t st.  fwd / inv apply the butterfly and its twiddles in registers exactly as
 // ct_stage does (same operations, same results).
-template <int R, int M, int L, int LGC, int PADS>
+template <int R, int M, int L, int NC, int PADS>
 struct CtStage {
     using B = typename Bfly<R>::type;
-    static constexpr unsigned total = (unsigned)(L / R) << LGC;   // butterflies of all columns
-    static constexpr unsigned mask = (1u << LGC) - 1u;
-    static constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : ((unsigned)M << LGC);
+    static constexpr unsigned total = (unsigned)(L / R) * NC;   // butterflies of all columns
+    static constexpr unsigned st = (PADS > 0 && M == PADS) ? (unsigned)M + 1 : (unsigned)M * NC;
     static constexpr unsigned tw_step = (unsigned)(L / (M * R));
     static __device__ __forceinline__ void locate(unsigned b, unsigned& nat, unsigned& j,
                                                   unsigned& col)
     {
-        col = b & mask;
-        const unsigned bi = b >> LGC;
+        col = b % (unsigned)NC;
+        const unsigned bi = b / (unsigned)NC;
         const unsigned blk = bi / (unsigned)M;
         j = bi - blk * (unsigned)M;
         nat = blk * (unsigned)M * R + j;
@@ -787,12 +786,12 @@ struct CtStage {
     {
         unsigned base = nat;
         if constexpr (PADS > 0) base += base / (unsigned)PADS;
-        return (base << LGC) + col;
+        return base * NC + col;
     }
     // the butterfly at buffer offset off stays inside the transform buffer
     static __device__ __forceinline__ bool in_buffer(unsigned off)
     {
-        constexpr unsigned limit = ((unsigned)L << LGC) + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
+        constexpr unsigned limit = (unsigned)L * NC + (PADS > 0 ? (unsigned)(L / PADS) : 0u);
         return BLFLS_DCHECK(off + (R - 1) * st < limit, kDcFftStage);
     }
     // forward (decimation in frequency): v in input order t -> out[q] = DFT(v)_q w^(j q)
@@ -848,36 +847,36 @@ __device__ __forceinline__ int ct_frequency(unsigned p)
     return ct_frequency_digits<P>(p, std::make_integer_sequence<int, P::nst>{});
 }
 
-// Stage s of plan P as a CtStage.
-template <class P, int S, int LGC, int PADS>
-using CtStageOf = CtStage<P::radix[S], P::span(S), P::L, LGC, PADS>;
+// Stage s of plan P as a CtStage (NC interleaved columns).
+template <class P, int S, int NC, int PADS>
+using CtStageOf = CtStage<P::radix[S], P::span(S), P::L, NC, PADS>;
 
 // Middle stages [S0, S1) of plan P through shared memory (forward, in order).
-template <class P, int LGC, int PADS, int S0, int... S>
+template <class P, int NC, int PADS, int S0, int... S>
 __device__ __forceinline__ void ct_forward_range(float2* x, const float2* tw,
                                                  std::integer_sequence<int, S...>)
 {
-    (ct_stage<P::radix[S0 + S], P::span(S0 + S), P::L, LGC, PADS, false>(x, tw), ...);
+    (ct_stage<P::radix[S0 + S], P::span(S0 + S), P::L, NC, PADS, false>(x, tw), ...);
 }
 // Inverse stages S1-1 .. S0 of plan P through shared memory (in the inverse order).
-template <class P, int LGC, int PADS, int S1, int... S>
+template <class P, int NC, int PADS, int S1, int... S>
 __device__ __forceinline__ void ct_inverse_range(float2* x, const float2* tw,
                                                  std::integer_sequence<int, S...>)
 {
-    (ct_stage<P::radix[S1 - 1 - S], P::span(S1 - 1 - S), P::L, LGC, PADS, true>(x, tw), ...);
+    (ct_stage<P::radix[S1 - 1 - S], P::span(S1 - 1 - S), P::L, NC, PADS, true>(x, tw), ...);
 }
 
 template <class P, int LGC, int PADS, int... S>
 __device__ __forceinline__ void ct_forward_stages(float2* x, const float2* tw,
                                                   std::integer_sequence<int, S...>)
 {
-    (ct_stage<P::radix[S], P::span(S), P::L, LGC, PADS, false>(x, tw), ...);
+    (ct_stage<P::radix[S], P::span(S), P::L, (1 << LGC), PADS, false>(x, tw), ...);
 }
 template <class P, int LGC, int PADS, int... S>
 __device__ __forceinline__ void ct_inverse_stages(float2* x, const float2* tw,
                                                   std::integer_sequence<int, S...>)
 {
-    (ct_stage<P::radix[P::nst - 1 - S], P::span(P::nst - 1 - S), P::L, LGC, PADS, true>(x, tw), ...);
+    (ct_stage<P::radix[P::nst - 1 - S], P::span(P::nst - 1 - S), P::L, (1 << LGC), PADS, true>(x, tw), ...);
 }
 
 // Forward / unnormalised inverse DFT of every column with plan P (PAD: a padded row buffer,

@@ -20,7 +20,7 @@ struct blfls_handle {
     int num_sms = 0;
     size_t budget = 0;  // 0 = unlimited
     size_t used = 0;
-    int col_block = 4;
+    int col_block = 4;   // K3 column block of the batched executor when none is tuned
     std::map<int, blfls::FftPlanHost> plans;
     // scratch (device)
     float* ex = nullptr;
@@ -111,6 +111,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t s);
 // Size the handle's batched-executor scratch arena up front (no reallocation later).
 int reserve_batch_scratch(blfls_handle* h, size_t bytes);
 int tuned_tile_h(const blfls_handle* h, int radius, int prec);
+// The tuned K3 column block for column length L, or 0 (none: the column driver's own choice).
 int tuned_col_block(const blfls_handle* h, int L);
 int load_tune_table(blfls_handle* h, const char* path);
 // The queue behind blfls_submit / blfls_poll (serve.cu): a server without a host-buffer arena

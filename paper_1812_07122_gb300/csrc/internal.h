@@ -139,8 +139,12 @@ cudaError_t launch_blf_batch(const BatchJob* jobs, const int2* grp, int ngrp, in
 struct SolveParams {
     int H, W;
     float lambda;
-    int col_block;   // columns per CTA in K3 (power of two, 1..16)
+    int col_block;   // columns per CTA in K3 (1..16; 0: the column driver's own choice)
 };
+
+// The K3 column block a solve launch takes for a requested col_block (0: the driver's own
+// choice) with column plan cp on an image W wide.
+int solve_effective_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms);
 
 // `marks` (nullable) receives two events recorded after K2 and after K3.
 cudaError_t launch_solve_residual(const float* f, const float* ex, const float* ey, float* out,

@@ -31,6 +31,8 @@ namespace {
 
 // Shared-memory budget of one solve CTA; twiddles share it with the data when they fit.
 constexpr size_t kSmemCap = 220 * 1024;
+// Column block of the staged column drivers when no tuned value is given.
+constexpr int kDefaultColBlock = 4;
 
 __device__ __forceinline__ const float2* stage_twiddles(float2* tw_smem, const FftPlanDev& p,
                                                         bool in_smem)
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
     constexpr int PADS = P::L / P::radix[0];
     constexpr int R0 = P::radix[0];
     constexpr unsigned M0 = P::span(0);
-    using S0 = CtStageOf<P, 0, 0, PADS>;
+    using S0 = CtStageOf<P, 0, 1, PADS>;
     extern __shared__ __align__(16) unsigned char staged_smem[];
     float* st = reinterpret_cast<float*>(staged_smem);
     const size_t Wp = row_floats(W);
@@ -609,7 +611,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
         }
         __syncthreads();
         if (p + 1 < p1) issue(p + 1);   // the rows of pair p have been read out
-        ct_forward_range<P, 0, PADS, 1>(data, rp.tw, std::make_integer_sequence<int, P::nst - 1>{});
+        ct_forward_range<P, 1, PADS, 1>(data, rp.tw, std::make_integer_sequence<int, P::nst - 1>{});
         float2* s0 = spec + (size_t)y0 * Wh;
         float2* s1 = spec + (size_t)(has1 ? y1 : y0) * Wh;
 #pragma unroll 4
@@ -625,7 +627,9 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
     }
 }
 
-template <int LGC, class P>
+// NC columns per block: any count, so that the column blocks can be balanced over the SMs (see
+// fused_col_block).
+template <int NC, class P>
 __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restrict__ spec, int H,
                                                                 int W, FftPlanDev cp,
                                                                 const float* __restrict__ sx,
@@ -636,13 +640,13 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
     constexpr unsigned M0 = P::span(0);
     constexpr int NL = P::nst - 1;
     constexpr int RL = P::radix[NL];
-    using S0 = CtStageOf<P, 0, LGC, 0>;
-    using SL = CtStageOf<P, NL, LGC, 0>;
+    using S0 = CtStageOf<P, 0, NC, 0>;
+    using SL = CtStageOf<P, NL, NC, 0>;
     extern __shared__ __align__(16) unsigned char staged_smem[];
     float2* data = reinterpret_cast<float2*>(staged_smem);
-    constexpr int CB = 1 << LGC;
+    constexpr int CB = NC;
     const int Wh = W / 2 + 1;
-    const int nblk = (Wh + CB - 1) >> LGC;
+    const int nblk = (Wh + CB - 1) / CB;
     const float2* tw = cp.tw;
     int b0, b1;
     band(nblk, b0, b1);
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
             for (int q = 0; q < R0; ++q) xb[q * S0::st] = o[q];
         }
         __syncthreads();
-        ct_forward_range<P, LGC, 0, 1>(data, tw, std::make_integer_sequence<int, NL - 1>{});
+        ct_forward_range<P, NC, 0, 1>(data, tw, std::make_integer_sequence<int, NL - 1>{});
         // last forward stage, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the
         // 1/(HW) of the inverse), first inverse stage -- all in registers
         for (unsigned b = threadIdx.x; b < SL::total; b += blockDim.x) {
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(kColThreadsMax) k3_cols_fused(float2* __restri
             for (int t = 0; t < RL; ++t) xb[t * SL::st] = o[t];
         }
         __syncthreads();
-        ct_inverse_range<P, LGC, 0, NL>(data, tw, std::make_integer_sequence<int, NL - 1>{});
+        ct_inverse_range<P, NC, 0, NL>(data, tw, std::make_integer_sequence<int, NL - 1>{});
         // last inverse stage, outputs to the spectrum in global memory
         for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
             unsigned nat, j, col;
@@ -727,8 +731,8 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2*
     constexpr unsigned M0 = P::span(0);
     constexpr int NL = P::nst - 1;
     constexpr int RL = P::radix[NL];
-    using S0 = CtStageOf<P, 0, 0, PADS>;
-    using SL = CtStageOf<P, NL, 0, PADS>;
+    using S0 = CtStageOf<P, 0, 1, PADS>;
+    using SL = CtStageOf<P, NL, 1, PADS>;
     extern __shared__ __align__(16) unsigned char staged_smem[];
     const int Wh = W / 2 + 1;
     const size_t Wp = row_floats(W);
@@ -789,7 +793,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2*
         __syncthreads();
         const bool more = p + 1 < p1;
         if (more) issue_spec(p + 1);  // the spectra of pair p have been read out
-        ct_inverse_range<P, 0, PADS, NL>(data, rp.tw, std::make_integer_sequence<int, NL - 1>{});
+        ct_inverse_range<P, 1, PADS, NL>(data, rp.tw, std::make_integer_sequence<int, NL - 1>{});
         if (more) cp_wait<1>(); else cp_wait<0>();   // f(p) landed
         __syncthreads();
         // last inverse stage (stage 0): u = f + result, real part row a, imaginary part row b
@@ -1115,22 +1119,31 @@ static ColsStagedFn cols_staged_kernel_p(int lgc)
     }
 }
 typedef void (*ColsFusedFn)(float2*, int, int, FftPlanDev, const float*, float, float);
+// Column counts the fused column driver is compiled for.  13 columns of 2160 points fill one
+// CTA's shared memory, and the 1921 columns of a 3840-wide spectrum then make 148 blocks: one
+// round over the 152 SMs.
+constexpr int kFusedBlocks[] = {1, 2, 4, 7, 8, 13, 16};
 template <class P>
-static ColsFusedFn cols_fused_kernel_p(int lgc)
+static ColsFusedFn cols_fused_kernel_p(int nc)
 {
-    switch (lgc) {
-        case 0: return k3_cols_fused<0, P>;
+    switch (nc) {
         case 1: return k3_cols_fused<1, P>;
         case 2: return k3_cols_fused<2, P>;
-        case 3: return k3_cols_fused<3, P>;
-        default: return k3_cols_fused<4, P>;
+        case 4: return k3_cols_fused<4, P>;
+        case 7: return k3_cols_fused<7, P>;
+        case 8: return k3_cols_fused<8, P>;
+        case 13: return k3_cols_fused<13, P>;
+        case 16: return k3_cols_fused<16, P>;
+        default: return nullptr;
     }
 }
-// The fused column driver of a compile-time plan, or nullptr (runtime plans: staged driver).
-static ColsFusedFn cols_fused_kernel(int lgc, const FftPlanDev& cp)
+static bool fused_plan(const FftPlanDev& cp) { return plan_is<ColPlanA>(cp) || plan_is<ColPlanB>(cp); }
+// The fused column driver of a compile-time plan for nc columns per block, or nullptr (runtime
+// plans: staged driver).
+static ColsFusedFn cols_fused_kernel(int nc, const FftPlanDev& cp)
 {
-    if (plan_is<ColPlanA>(cp)) return cols_fused_kernel_p<ColPlanA>(lgc);
-    if (plan_is<ColPlanB>(cp)) return cols_fused_kernel_p<ColPlanB>(lgc);
+    if (plan_is<ColPlanA>(cp)) return cols_fused_kernel_p<ColPlanA>(nc);
+    if (plan_is<ColPlanB>(cp)) return cols_fused_kernel_p<ColPlanB>(nc);
     return nullptr;
 }
 static ColsStagedFn cols_staged_kernel(int lgc, const FftPlanDev& cp)
@@ -1138,8 +1151,33 @@ static ColsStagedFn cols_staged_kernel(int lgc, const FftPlanDev& cp)
     (void)cp;
     return cols_staged_kernel_p<void>(lgc);
 }
-// Shared memory of the fused column driver: one column block.
-static size_t k3f_smem(int L, int lgc) { return sizeof(float2) * ((size_t)L << lgc); }
+// Shared memory of the fused column driver: one block of nc columns.
+static size_t k3f_smem(int L, int nc) { return sizeof(float2) * (size_t)L * nc; }
+
+// Columns per block of the fused column driver.  A block size from a tune table (col_block > 0)
+// is taken as the largest compiled count not above it that fits; otherwise the count that
+// minimises ceil(blocks / SMs) x columns per block (the columns the busiest SM transforms), the
+// larger count winning ties.
+static int fused_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms)
+{
+    const int ncols = W / 2 + 1;
+    int best = 1;
+    long best_cost = -1;
+    for (int nc : kFusedBlocks) {
+        if (k3f_smem(cp.L, nc) > kSmemCap) continue;
+        if (col_block > 0) {
+            if (nc <= col_block) best = nc;
+            continue;
+        }
+        const long blocks = (ncols + nc - 1) / nc;
+        const long cost = (blocks + num_sms - 1) / num_sms * nc;
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best = nc;
+        }
+    }
+    return best;
+}
 
 static void set_staged_attributes()
 {
@@ -1148,16 +1186,16 @@ static void set_staged_attributes()
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     for (RowsK4Fn f : {k4_rows_staged<void>, k4_rows_fused<RowPlanA>, k4_rows_fused<RowPlanB>})
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    for (int lgc = 0; lgc <= 4; ++lgc) {
+    for (int lgc = 0; lgc <= 4; ++lgc)
         cudaFuncSetAttribute(cols_staged_kernel_p<void>(lgc),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        for (ColsFusedFn f : {cols_fused_kernel_p<ColPlanA>(lgc), cols_fused_kernel_p<ColPlanB>(lgc)})
+    for (int nc : kFusedBlocks)
+        for (ColsFusedFn f : {cols_fused_kernel_p<ColPlanA>(nc), cols_fused_kernel_p<ColPlanB>(nc)})
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    }
 }
 
 // Block size of a column driver (fn: its kernel); see the comment above.
-static int col_threads(const void* fn, const FftPlanDev& cp, int lgc, size_t smem, int* occ_out)
+static int col_threads(const void* fn, const FftPlanDev& cp, int ncol, size_t smem, int* occ_out)
 {
     int best_t = 128, best_occ = 1;
     double best = 1e30;
@@ -1167,7 +1205,7 @@ static int col_threads(const void* fn, const FftPlanDev& cp, int lgc, size_t sme
         if (occ < 1) continue;
         long rounds = 0;
         for (int st = 0; st < cp.nst; ++st) {
-            const long nb = (long)(cp.L / cp.radix[st]) << lgc;
+            const long nb = (long)(cp.L / cp.radix[st]) * ncol;
             rounds += (nb + t - 1) / t;
         }
         const double cost = (double)rounds / occ;
@@ -1175,6 +1213,14 @@ static int col_threads(const void* fn, const FftPlanDev& cp, int lgc, size_t sme
     }
     *occ_out = best_occ;
     return best_t;
+}
+
+int solve_effective_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms)
+{
+    if (fused_plan(cp)) return fused_col_block(cp, W, col_block, num_sms);
+    int lgc = solve_fit_lgc(cp.L, col_block > 0 ? col_block : kDefaultColBlock);
+    while (lgc > 0 && k3s_smem(cp.L, lgc) > kSmemCap) --lgc;
+    return 1 << lgc;
 }
 
 cudaError_t launch_solve_residual(const float* f, const float* ex, const float* ey, float* out,
@@ -1190,11 +1236,13 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     const bool al16 = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(ex) | reinterpret_cast<uintptr_t>(ey) |
                                         reinterpret_cast<uintptr_t>(f)) % 16 == 0);
     const bool rows_staged = k2s_smem(W, rp) <= cap && k4s_smem(W, rp) <= cap;
-    int lgc = solve_fit_lgc(cp.L, p.col_block);
-    const ColsFusedFn k3f = cols_fused_kernel(lgc, cp);
-    if (!k3f)
-        while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
-    const bool cols_fused = k3f != nullptr && k3f_smem(cp.L, lgc) <= cap;
+    // the fused column driver on compile-time plans (any column count, see fused_col_block),
+    // else the staged driver on a power-of-two block (col_block 0: no tuned value, the default)
+    const int nc = fused_plan(cp) ? fused_col_block(cp, W, p.col_block, num_sms) : 0;
+    const ColsFusedFn k3f = nc > 0 ? cols_fused_kernel(nc, cp) : nullptr;
+    const bool cols_fused = k3f != nullptr && k3f_smem(cp.L, nc) <= cap;
+    int lgc = solve_fit_lgc(cp.L, p.col_block > 0 ? p.col_block : kDefaultColBlock);
+    while (lgc > 0 && k3s_smem(cp.L, lgc) > cap) --lgc;
     const bool cols_staged = !cols_fused && k3s_smem(cp.L, lgc) <= cap;
     const int CB = 1 << lgc;
     const int npairs = (H + 1) / 2;
@@ -1218,20 +1266,21 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
     }
     if (marks) cudaEventRecord(marks[0], s);
     if (cols_fused) {
-        const size_t sm3 = k3f_smem(cp.L, lgc);
+        const size_t sm3 = k3f_smem(cp.L, nc);
         int occ = 0;
-        const int thr = col_threads((const void*)k3f, cp, lgc, sm3, &occ);
-        const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
+        const int thr = col_threads((const void*)k3f, cp, nc, sm3, &occ);
+        const int nblk_f = (W / 2 + 1 + nc - 1) / nc;
+        const int grid = std::max(1, std::min(nblk_f, num_sms * std::max(occ, 1)));
         k3f<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, p.lambda, scale);
     } else if (cols_staged) {
         const size_t sm3 = k3s_smem(cp.L, lgc);
         int occ = 0;
         const ColsStagedFn k3 = cols_staged_kernel(lgc, cp);
-        const int thr = col_threads((const void*)k3, cp, lgc, sm3, &occ);
+        const int thr = col_threads((const void*)k3, cp, 1 << lgc, sm3, &occ);
         const int grid = std::max(1, std::min(nblk, num_sms * std::max(occ, 1)));
         k3<<<grid, thr, sm3, s>>>(spec, H, W, cp, sx, sy, p.lambda, scale);
     } else {
-        const int lgc1 = solve_fit_lgc(cp.L, p.col_block);
+        const int lgc1 = solve_fit_lgc(cp.L, p.col_block > 0 ? p.col_block : kDefaultColBlock);
         const int CB1 = 1 << lgc1;
         const size_t smem_c = solve_smem_cols(cp, CB1);
         const int tw_c = smem_c > sizeof(float2) * (size_t)cp.L * CB1;

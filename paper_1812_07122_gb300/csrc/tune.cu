@@ -11,6 +11,7 @@
 // speed only, never results (the arithmetic per pixel is the same for every shape).
 #include "handle.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,7 +70,7 @@ int tuned_tile_h(const blfls_handle* h, int radius, int prec)
 int tuned_col_block(const blfls_handle* h, int L)
 {
     auto it = h->tune_col_block.find(log2_class(L));
-    return it == h->tune_col_block.end() ? h->col_block : it->second;
+    return it == h->tune_col_block.end() ? 0 : it->second;
 }
 
 int load_tune_table(blfls_handle* h, const char* path)
@@ -185,10 +186,14 @@ extern "C" int blfls_autotune(blfls_handle* h, int H, int W, int C, int radius, 
         float2* spec = nullptr;
         e = cudaMalloc(&spec, sizeof(float2) * (size_t)H * (W / 2 + 1));
         if (e == cudaSuccess) {
-            int best_cb = h->col_block;
+            int best_cb = 0;
             float best_ms = 1e30f;
-            for (int cb = 1; cb <= 16; cb *= 2) {
-                if ((1 << solve_fit_lgc(cp->L, cb)) != cb) continue;   // does not fit
+            std::vector<int> timed;
+            for (int cb : {1, 2, 4, 7, 8, 13, 16}) {
+                // each block size a column driver really takes, once
+                const int eff = solve_effective_col_block(*cp, W, cb, h->num_sms);
+                if (eff != cb || std::find(timed.begin(), timed.end(), eff) != timed.end()) continue;
+                timed.push_back(eff);
                 const SolveParams sp{H, W, 30.0f, cb};
                 const float ms = time_it([&] {
                     launch_solve_residual(img, ex, ey, img + 0 * n, spec, *rp, *cp, rp->lap,
@@ -199,7 +204,7 @@ extern "C" int blfls_autotune(blfls_handle* h, int H, int W, int C, int radius, 
                     best_cb = cb;
                 }
             }
-            h->tune_col_block[log2_class(cp->L)] = best_cb;
+            if (best_cb > 0) h->tune_col_block[log2_class(cp->L)] = best_cb;
             cudaFree(spec);
         } else {
             cudaGetLastError();

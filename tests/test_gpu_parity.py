@@ -82,9 +82,10 @@ def test_solve_residual_matches_eq8(h, H, W, lam):
                                           (9, 1920, 4)])
 def test_solve_compile_time_plans_every_column_block(tmp_path, H, W, log2_len):
     """The lengths with compile-time plans (columns of 2160 and 1080, rows of 3840 and 1920),
-    with every column block the column driver can take (chosen through a tune table): each
-    matches Eq. 8, and all blocks give the same bits (a column's arithmetic does not depend on
-    how columns are grouped)."""
+    with every column block the column driver can take (chosen through a tune table; 16
+    columns of 2160 points exceed the shared-memory budget and run as 13) and with the driver's
+    own choice (an empty table): each matches Eq. 8, and all blocks give the same bits (a
+    column's arithmetic does not depend on how columns are grouped)."""
     import json
     rng = np.random.default_rng(H * 7 + W)
     f = rng.uniform(size=(H, W)).astype(np.float32)
@@ -93,10 +94,11 @@ def test_solve_compile_time_plans_every_column_block(tmp_path, H, W, log2_len):
     gx, gy = oracle.gradients(f)
     want = oracle.solve_eq8(f, gx + ex.astype(np.float64), gy + ey.astype(np.float64), 30.0)
     outs = []
-    for cb in (1, 2, 4, 8, 16):
+    for cb in (1, 2, 4, 7, 8, 13, 16, None):
         path = tmp_path / f"tune_{cb}.json"
+        blocks = [] if cb is None else [{"log2_len": log2_len, "col_block": cb}]
         path.write_text(json.dumps({"blfls_tune_table": 1, "k1_tile_h": [],
-                                    "k3_col_block": [{"log2_len": log2_len, "col_block": cb}]}))
+                                    "k3_col_block": blocks}))
         h2 = blfls.blfls_create(0, tune_table_path=str(path))
         try:
             outs.append(solve_residual(h2, f, ex, ey, 30.0)[0])
