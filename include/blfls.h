@@ -185,6 +185,7 @@ int blfls_smooth_normalized(blfls_handle *h, const float *img, float *out, int H
 /* ---- BLF-LS with the bilateral-grid filter (the fast approximation the paper uses) -------- */
 
 #define BLFLS_GRID_MAX_BYTES (8ull << 30)
+#define BLFLS_GRID_MAX_RANGE_CELLS 65536
 
 /* BLF-LS (Eqs. 7-8) with each gradient field filtered by the bilateral-grid approximation of
  * Eq. 1 (Paris and Durand's fast bilateral filter, which the paper's experiments use,
@@ -192,11 +193,14 @@ int blfls_smooth_normalized(blfls_handle *h, const float *img, float *out, int H
  * padding, splat to the nearest cell, 3-tap Gaussian blur of one cell along each grid axis,
  * trilinear slice; open image borders in the grid (the solve stays periodic).  FP32; a pixel's
  * cell is floor(t + 1/2) of the real value t of its coordinates for its FP32 gradient (taken in
- * FP64 where the FP32 value is near a rounding boundary).  Device
- * pointers [C][H][W]; out may equal img.  Each pass reads the fields' ranges back to the host
- * to size the grid, so the call synchronises `stream` once per pass.  sigma_s must be finite and
- * >= 0.5; sigma_r may be +inf (one range cell).  Errors: BLFLS_EINVAL (arguments as
- * blfls_smooth without radius and precision, sigma_s out of range, a grid above
+ * FP64 where the FP32 value is near a rounding boundary).  Device pointers [C][H][W]; out may
+ * equal img; asynchronous on `stream` (the fields' ranges, which fix the number of range cells,
+ * stay on the device: the grid buffers hold a chunk of range levels sized from sigma_r for
+ * fields of range up to 2, and a wider field is filtered chunk by chunk with the same result).
+ * A field whose range spans more than BLFLS_GRID_MAX_RANGE_CELLS cells of sigma_r, or holds a
+ * NaN, cannot be gridded: its channel's output is NaN.  sigma_s must be finite and >= 0.5;
+ * sigma_r may be +inf (one range cell).  Errors: BLFLS_EINVAL (arguments as blfls_smooth
+ * without radius and precision, sigma_s out of range, grid buffers above
  * BLFLS_GRID_MAX_BYTES), BLFLS_ENOMEM, BLFLS_ECUDA. */
 int blfls_smooth_grid(blfls_handle *h, const float *img, float *out, int H, int W, int C,
                       float lambda, float sigma_s, float sigma_r, int iters, void *stream);

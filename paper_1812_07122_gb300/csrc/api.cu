@@ -525,7 +525,6 @@ void blfls_destroy(blfls_handle* h)
     if (h->gtmp) cudaFree(h->gtmp);
     if (h->grid_a) cudaFree(h->grid_a);
     if (h->grid_keys) cudaFree(h->grid_keys);
-    if (h->grid_keys_host) cudaFreeHost(h->grid_keys_host);
     if (h->kap_dev) cudaFree(h->kap_dev);
     if (h->nc_scratch) cudaFree(h->nc_scratch);
     if (h->chan_scratch) cudaFree(h->chan_scratch);
@@ -840,41 +839,25 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
     if ((rc = prepare(h, H, W, 0, false, true, &rp, &cp)) != BLFLS_OK) return rc;
     if ((rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "grid keys")) != BLFLS_OK)
         return rc;
-    if (!h->grid_keys_host) {
-        void* p = nullptr;
-        const cudaError_t e = cudaMallocHost(&p, sizeof(int) * 4 * BLFLS_MAX_CHANNELS);
-        if (e != cudaSuccess) return cuda_fail(e, "pinned grid keys");
-        h->grid_keys_host = static_cast<int*>(p);
-    }
+    // the buffers hold one chunk of range levels; a wider range takes more chunks on the device
+    int gx = 0, gy = 0;
+    grid_spatial_dims(H, W, sigma_s, &gx, &gy);
+    const int zc = grid_chunk_levels(sigma_r, gx, gy);
+    const size_t cells = (size_t)gx * gy * (size_t)(zc + 2);
+    if (2 * cells * sizeof(float2) > BLFLS_GRID_MAX_BYTES)
+        return fail(BLFLS_EINVAL, "bilateral grid above BLFLS_GRID_MAX_BYTES: raise sigma_s or sigma_r");
+    if ((rc = ensure_grid(h, cells)) != BLFLS_OK) return rc;
     const SolveParams sp{H, W, lambda, tuned_col_block(h, cp->L)};
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
-        // the ranges of both fields of every channel size the grids of this pass
         cudaError_t e = launch_grid_minmax(src, H, W, C, h->grid_keys, s, h->num_sms);
         if (e != cudaSuccess) return cuda_fail(e, "grid range kernel launch");
-        e = cudaMemcpyAsync(h->grid_keys_host, h->grid_keys, sizeof(int) * 4 * C,
-                            cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "grid range read-back");
-        float lo[2 * BLFLS_MAX_CHANNELS];
-        int dims[2 * BLFLS_MAX_CHANNELS][3];
-        size_t cells = 0;
-        for (int q = 0; q < 2 * C; ++q) {
-            lo[q] = grid_key_to_float(h->grid_keys_host[2 * q]);
-            const float hi = grid_key_to_float(h->grid_keys_host[2 * q + 1]);
-            grid_dims(H, W, lo[q], hi, sigma_s, sigma_r, &dims[q][0], &dims[q][1], &dims[q][2]);
-            cells = std::max(cells, (size_t)dims[q][0] * dims[q][1] * dims[q][2]);
-        }
-        if (2 * cells * sizeof(float2) > BLFLS_GRID_MAX_BYTES)
-            return fail(BLFLS_EINVAL, "bilateral grid above BLFLS_GRID_MAX_BYTES: raise sigma_s or sigma_r");
-        if ((rc = ensure_grid(h, cells)) != BLFLS_OK) return rc;
         for (int c = 0; c < C; ++c) {
             const float* fc = src + c * plane;
             for (int field = 0; field < 2; ++field) {
-                const int q = 2 * c + field;
-                e = launch_grid_residual(fc, field == 0 ? h->ex : h->ey, field, H, W, sigma_s,
-                                         sigma_r, lo[q], dims[q][0], dims[q][1], dims[q][2],
-                                         h->grid_a, h->grid_b, s, h->num_sms);
+                e = launch_grid_field(fc, field == 0 ? h->ex : h->ey, field, H, W, sigma_s,
+                                      sigma_r, h->grid_keys + 4 * c + 2 * field, gx, gy, zc,
+                                      h->grid_a, h->grid_b, s, h->num_sms);
                 if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
             }
             e = solve_launch(h, fc, h->ex, h->ey, out + c * plane, *rp, *cp, sp, s);
@@ -884,20 +867,12 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
     return BLFLS_OK;
 }
 
-// Pinned and device room for the per-pass range read-back of both fields of every channel.
+// Device room for the range keys and range constants of both fields of every channel.
 static int ensure_range_keys(blfls_handle* h)
 {
     int rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "range keys");
     if (rc != BLFLS_OK) return rc;
-    rc = grow(h, h->kap_dev, h->kap_cap, (size_t)BLFLS_MAX_CHANNELS, "range constants");
-    if (rc != BLFLS_OK) return rc;
-    if (!h->grid_keys_host) {
-        void* p = nullptr;
-        const cudaError_t e = cudaMallocHost(&p, sizeof(int) * 4 * BLFLS_MAX_CHANNELS);
-        if (e != cudaSuccess) return cuda_fail(e, "pinned range keys");
-        h->grid_keys_host = static_cast<int*>(p);
-    }
-    return BLFLS_OK;
+    return grow(h, h->kap_dev, h->kap_cap, (size_t)BLFLS_MAX_CHANNELS, "range constants");
 }
 
 int blfls_smooth_normalized(blfls_handle* h, const float* img, float* out, int H, int W, int C,

@@ -6,12 +6,16 @@
 // a padding of P = 2 cells, the grid holds (sum of g, count) pairs over
 // Gz x Gy x Gx = (floor((max g - min g) / s_r) + 1 + 2P) x (floor((H-1)/s_s) + 1 + 2P) x
 // (floor((W-1)/s_s) + 1 + 2P) cells, z-major:
-//   k6_minmax   min and max of both fields of every channel (order-preserving integer keys, so the
-//               atomics are exact and the result does not depend on their order);
-//   k6_splat    one thread per spatial cell walks the pixels whose nearest cell it is and adds
-//               (g, 1) to the range bin of each, in a fixed order (deterministic, no atomics);
-//   k6_blur     the 3-tap kernel (e^-1/2, 1, e^-1/2) along x, y, then z (zero outside);
-//   k6_slice    trilinear interpolation at (z, y / s_s + P, x / s_s + P): e = sum / count - g.
+//   k6_minmax      min and max of both fields of every channel (order-preserving integer keys, so
+//                  the atomics are exact and the result does not depend on their order);
+//   k6_grid_field  one cooperative launch per field: Gz from the keys on the device, then, chunk
+//                  by chunk of range levels: splat (one thread per spatial cell walks the pixels
+//                  whose nearest cell it is and adds (g, 1) to the range level of each, in a fixed
+//                  order: deterministic, no atomics), the 3-tap blur (e^-1/2, 1, e^-1/2) along x,
+//                  y, then z (zero outside), and the trilinear slice at (z, y / s_s + P,
+//                  x / s_s + P): e = sum / count - g.
+// The range is never read back to the host: the buffers hold a chunk of levels whose size the
+// host fixes, and a wider range takes more chunks.
 // Cell indices are floor(t + 1/2) of the real t: FP32 decides away from rounding boundaries, FP64
 // near them (see cell_of), so the cells are those of the FP64 definition on the FP32 gradients.
 // Grid passes are HBM/L2-bound streams.
@@ -20,10 +24,15 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
+#include "blfls.h"
 #include "dcheck.cuh"
 #include "internal.h"
 
 namespace blfls {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -78,10 +87,25 @@ __global__ void __launch_bounds__(kGridThreads) k6_minmax(const float* __restric
     }
 }
 
-struct GridGeom {
-    int H, W, gx, gy, gz;
-    float ss, sr, lo;
-    int field;
+__device__ __forceinline__ float key_to_float(int key)
+{
+    return __int_as_float(key ^ ((key >> 31) & 0x7fffffff));
+}
+
+// One field's grid, computed in chunks of range levels so that the buffers have a size the host
+// knows before the range is known: chunk k holds the levels z in [zb - 1, zb + zc] of the grid
+// (zb = k (zc - 1); buffer level l = z - zb + 1), and slices the pixels whose lower trilinear
+// level z0 lies in [zb, zb + zc - 1), so the chunks partition the pixels.  Every cell of a chunk
+// is the same sum, blurred in the same order, as in the whole grid (the levels just outside a
+// chunk are splatted too), so the result does not depend on zc.
+struct GridChunk {
+    const float* f;
+    float* e;
+    const int* keys;    // order-preserving min / max keys of this field (launch_grid_minmax)
+    float2* ga;
+    float2* gb;         // (zc + 2) x gy x gx cells each
+    int H, W, gx, gy, zc, field;
+    float ss, sr;
 };
 
 // floor((a - b) / den + 1/2) of the exact real value for FP32 operands: the FP32 evaluation
@@ -97,31 +121,33 @@ __device__ __forceinline__ int cell_of(float a, float b, float den)
     return (int)floor(__dadd_rn(__ddiv_rn(__dsub_rn((double)a, (double)b), (double)den), 0.5));
 }
 
-// One thread per spatial cell (cy, cx) that a pixel can round to: floor((W-1)/s_s) + 2 cells per
-// axis (the last pixel can round up into the first padding cell).
-__global__ void __launch_bounds__(kGridThreads) k6_splat(const float* __restrict__ f,
-                                                        float2* __restrict__ grid, GridGeom G)
+// Splat: one thread per spatial cell (cy, cx) that a pixel can round to (floor((W-1)/s_s) + 2
+// cells per axis: the last pixel can round up into the first padding cell) walks its pixels in
+// order and adds (g, 1) to the range level of each that falls in the chunk.
+__device__ __forceinline__ void grid_splat(const GridChunk& P, float lo, int gz, int zb,
+                                           size_t tid, size_t nthreads)
 {
-    const int nx = G.gx - 2 * kPad + 1, ny = G.gy - 2 * kPad + 1;
-    const size_t slab = (size_t)G.gy * G.gx;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nx * ny; t += gridDim.x * blockDim.x) {
-        const int ky = t / nx, kx = t - ky * nx;
+    const int nx = P.gx - 2 * kPad + 1, ny = P.gy - 2 * kPad + 1;
+    const size_t slab = (size_t)P.gy * P.gx;
+    for (size_t t = tid; t < (size_t)nx * ny; t += nthreads) {
+        const int ky = (int)(t / nx), kx = (int)(t - (size_t)ky * nx);
         // candidates around (k - 1/2) s .. (k + 1/2) s; each checked with the cell decision itself
-        const int y0 = max(0, (int)floorf((ky - 0.5f) * G.ss) - 1);
-        const int y1 = min(G.H - 1, (int)ceilf((ky + 0.5f) * G.ss) + 1);
-        const int x0 = max(0, (int)floorf((kx - 0.5f) * G.ss) - 1);
-        const int x1 = min(G.W - 1, (int)ceilf((kx + 0.5f) * G.ss) + 1);
-        float2* col = grid + (size_t)(ky + kPad) * G.gx + (kx + kPad);
+        const int y0 = max(0, (int)floorf((ky - 0.5f) * P.ss) - 1);
+        const int y1 = min(P.H - 1, (int)ceilf((ky + 0.5f) * P.ss) + 1);
+        const int x0 = max(0, (int)floorf((kx - 0.5f) * P.ss) - 1);
+        const int x1 = min(P.W - 1, (int)ceilf((kx + 0.5f) * P.ss) + 1);
+        float2* col = P.ga + (size_t)(ky + kPad) * P.gx + (kx + kPad);
         for (int y = y0; y <= y1; ++y) {
-            if (cell_of((float)y, 0.0f, G.ss) != ky) continue;
+            if (cell_of((float)y, 0.0f, P.ss) != ky) continue;
             for (int x = x0; x <= x1; ++x) {
-                if (cell_of((float)x, 0.0f, G.ss) != kx) continue;
-                const float g = grad_at(f, G.H, G.W, y, x, G.field);
-                const int z = cell_of(g, G.lo, G.sr) + kPad;
-                if (!BLFLS_DCHECK(z >= 0 && z < G.gz && ky + kPad < G.gy && kx + kPad < G.gx,
+                if (cell_of((float)x, 0.0f, P.ss) != kx) continue;
+                const float g = grad_at(P.f, P.H, P.W, y, x, P.field);
+                const int l = cell_of(g, lo, P.sr) + kPad - zb + 1;
+                if (l < 0 || l > P.zc + 1) continue;   // another chunk's level
+                if (!BLFLS_DCHECK(l - 1 + zb < gz && ky + kPad < P.gy && kx + kPad < P.gx,
                                   kDcGridCell))
                     continue;
-                float2* c = col + (size_t)z * slab;
+                float2* c = col + (size_t)l * slab;
                 c->x += g;
                 c->y += 1.f;
             }
@@ -129,18 +155,31 @@ __global__ void __launch_bounds__(kGridThreads) k6_splat(const float* __restrict
     }
 }
 
-// out[i] = in[i] + e (in[i - stride] + in[i + stride]) along one axis (zero outside).
-__global__ void __launch_bounds__(kGridThreads) k6_blur(const float2* __restrict__ in,
-                                                       float2* __restrict__ out, int gx, int gy,
-                                                       int gz, int axis)
+// out = in + e (in[-stride] + in[+stride]) along x (axis 0) or y (axis 1) of every level, or
+// along z (axis 2) for the chunk's interior levels; zero outside the whole grid.
+__device__ __forceinline__ void grid_blur(const float2* __restrict__ in, float2* __restrict__ out,
+                                          const GridChunk& P, int gz, int zb, int axis,
+                                          size_t tid, size_t nthreads)
 {
     const float e = 0.60653065971263342f;   // exp(-1/2)
-    const size_t n = (size_t)gx * gy * gz;
-    const size_t stride = axis == 0 ? 1 : axis == 1 ? (size_t)gx : (size_t)gx * gy;
-    const int len = axis == 0 ? gx : axis == 1 ? gy : gz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int pos = (int)((i / stride) % (size_t)len);
+    const size_t slab = (size_t)P.gx * P.gy;
+    const size_t first = axis == 2 ? slab : 0;
+    const size_t n = axis == 2 ? slab * (size_t)P.zc : slab * (size_t)(P.zc + 2);
+    const size_t stride = axis == 0 ? 1 : axis == 1 ? (size_t)P.gx : slab;
+    for (size_t k = tid; k < n; k += nthreads) {
+        const size_t i = first + k;
+        int pos, len;
+        if (axis == 0) {
+            pos = (int)(i % (size_t)P.gx);
+            len = P.gx;
+        } else if (axis == 1) {
+            pos = (int)((i / (size_t)P.gx) % (size_t)P.gy);
+            len = P.gy;
+        } else {
+            pos = (int)(i / slab) - 1 + zb;   // global level
+            len = gz;
+            if (pos >= gz) continue;          // beyond the grid: never sliced
+        }
         float2 a = in[i];
         float2 s = make_float2(0.f, 0.f);
         if (pos > 0) { const float2 b = in[i - stride]; s.x += b.x; s.y += b.y; }
@@ -149,21 +188,24 @@ __global__ void __launch_bounds__(kGridThreads) k6_blur(const float2* __restrict
     }
 }
 
-__global__ void __launch_bounds__(kGridThreads) k6_slice(const float* __restrict__ f,
-                                                        const float2* __restrict__ grid,
-                                                        float* __restrict__ e, GridGeom G)
+// Slice: trilinear interpolation at (z, y / s_s + P, x / s_s + P) for the pixels whose lower
+// level z0 lies in [zb, zb + zc - 1): e = sum / count - g.
+__device__ __forceinline__ void grid_slice(const GridChunk& P, float lo, int gz, int zb,
+                                           size_t tid, size_t nthreads)
 {
-    const size_t plane = (size_t)G.H * G.W;
-    const size_t slab = (size_t)G.gy * G.gx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / G.W), x = (int)(i - (size_t)y * G.W);
-        const float g = grad_at(f, G.H, G.W, y, x, G.field);
-        const float zf = __fdiv_rn(g - G.lo, G.sr) + kPad;
-        const float yf = __fdiv_rn((float)y, G.ss) + kPad;
-        const float xf = __fdiv_rn((float)x, G.ss) + kPad;
-        const int z0 = min((int)zf, G.gz - 2), y0 = min((int)yf, G.gy - 2), x0 = min((int)xf, G.gx - 2);
+    const size_t plane = (size_t)P.H * P.W;
+    const size_t slab = (size_t)P.gy * P.gx;
+    for (size_t i = tid; i < plane; i += nthreads) {
+        const int y = (int)(i / P.W), x = (int)(i - (size_t)y * P.W);
+        const float g = grad_at(P.f, P.H, P.W, y, x, P.field);
+        const float zf = __fdiv_rn(g - lo, P.sr) + kPad;
+        const int z0 = min((int)zf, gz - 2);
+        if (z0 < zb || z0 >= zb + P.zc - 1) continue;   // another chunk's pixel
+        const float yf = __fdiv_rn((float)y, P.ss) + kPad;
+        const float xf = __fdiv_rn((float)x, P.ss) + kPad;
+        const int y0 = min((int)yf, P.gy - 2), x0 = min((int)xf, P.gx - 2);
         const float fz = zf - z0, fy = yf - y0, fx = xf - x0;
+        const float2* base = P.gb + (size_t)(z0 - zb + 1) * slab;
         float sw = 0.f, sc = 0.f;
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
@@ -172,17 +214,51 @@ __global__ void __launch_bounds__(kGridThreads) k6_slice(const float* __restrict
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const float w = (dz ? fz : 1.f - fz) * (dy ? fy : 1.f - fy) * (dx ? fx : 1.f - fx);
-                    const float2 c = grid[(size_t)(z0 + dz) * slab + (size_t)(y0 + dy) * G.gx + (x0 + dx)];
+                    const float2 c = base[(size_t)dz * slab + (size_t)(y0 + dy) * P.gx + (x0 + dx)];
                     sw = fmaf(w, c.x, sw);
                     sc = fmaf(w, c.y, sc);
                 }
-        e[i] = __fdiv_rn(sw, sc) - g;
+        P.e[i] = __fdiv_rn(sw, sc) - g;
     }
 }
 
-__device__ __forceinline__ float key_to_float(int key)
+// The whole grid filter of one field in one cooperative launch: the range levels follow from the
+// field's range keys on the device (no read-back), then for each chunk: clear, splat, blur x, y, z,
+// slice, with a grid-wide barrier between the phases.  Every block takes the same branches, so
+// every block reaches every barrier.  A range of more than max_cells cells of sigma_r (or a NaN
+// range) gives NaN residuals for the field.
+__global__ void __launch_bounds__(kGridThreads) k6_grid_field(GridChunk P, int max_cells)
 {
-    return __int_as_float(key ^ ((key >> 31) & 0x7fffffff));
+    cg::grid_group grid = cg::this_grid();
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+    const float lo = key_to_float(P.keys[0]);
+    const float hi = key_to_float(P.keys[1]);
+    // the number of range cells, as the FP64 definition floor((max - min) / s_r) + 1 + 2P
+    const double span = floor(((double)hi - (double)lo) / (double)P.sr);
+    if (!(span >= 0.0 && span <= (double)max_cells)) {
+        const size_t plane = (size_t)P.H * P.W;
+        for (size_t i = tid; i < plane; i += nthreads) P.e[i] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int gz = (int)span + 1 + 2 * kPad;
+    const int nchunks = (gz - 1 + P.zc - 2) / (P.zc - 1);   // chunks of z0 in [0, gz - 2]
+    const size_t cells = (size_t)P.gx * P.gy * (size_t)(P.zc + 2);
+    for (int k = 0; k < nchunks; ++k) {
+        const int zb = k * (P.zc - 1);
+        for (size_t i = tid; i < cells; i += nthreads) P.ga[i] = make_float2(0.f, 0.f);
+        grid.sync();
+        grid_splat(P, lo, gz, zb, tid, nthreads);
+        grid.sync();
+        grid_blur(P.ga, P.gb, P, gz, zb, 0, tid, nthreads);
+        grid.sync();
+        grid_blur(P.gb, P.ga, P, gz, zb, 1, tid, nthreads);
+        grid.sync();
+        grid_blur(P.ga, P.gb, P, gz, zb, 2, tid, nthreads);
+        grid.sync();
+        grid_slice(P, lo, gz, zb, tid, nthreads);
+        grid.sync();
+    }
 }
 
 // Range constants of every channel for normalised gradients: each field's range R = max - min
@@ -241,31 +317,36 @@ float grid_key_to_float(int key)
     return v;
 }
 
-void grid_dims(int H, int W, float lo, float hi, float sigma_s, float sigma_r, int* gx, int* gy,
-               int* gz)
+void grid_spatial_dims(int H, int W, float sigma_s, int* gx, int* gy)
 {
-    const double ss = sigma_s, sr = sigma_r;
+    const double ss = sigma_s;
     *gx = (int)std::floor((W - 1) / ss) + 1 + 2 * kPad;
     *gy = (int)std::floor((H - 1) / ss) + 1 + 2 * kPad;
-    *gz = (int)std::floor(((double)hi - (double)lo) / sr) + 1 + 2 * kPad;
 }
 
-cudaError_t launch_grid_residual(const float* f, float* e, int field, int H, int W, float sigma_s,
-                                 float sigma_r, float lo, int gx, int gy, int gz, float2* ga,
-                                 float2* gb, cudaStream_t s, int num_sms)
+int grid_chunk_levels(float sigma_r, int gx, int gy)
 {
-    const size_t cells = (size_t)gx * gy * gz;
-    cudaError_t err = cudaMemsetAsync(ga, 0, cells * sizeof(float2), s);
+    // the levels a field of range 2 needs (gradients of an image in [0, 1]), at most 256 MiB of
+    // cells per buffer, at least 8
+    const double want = std::floor(2.0 / (double)sigma_r) + 1 + 2 * kPad;
+    const double budget = std::floor((256.0 * 1024 * 1024) / (sizeof(float2) * (double)gx * gy)) - 2;
+    return (int)std::max(8.0, std::min(want, budget));
+}
+
+cudaError_t launch_grid_field(const float* f, float* e, int field, int H, int W, float sigma_s,
+                              float sigma_r, const int* keys, int gx, int gy, int zc, float2* ga,
+                              float2* gb, cudaStream_t s, int num_sms)
+{
+    const GridChunk P{f, e, keys, ga, gb, H, W, gx, gy, zc, field, sigma_s, sigma_r};
+    int max_cells = BLFLS_GRID_MAX_RANGE_CELLS;
+    int occ = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_grid_field,
+                                                                     kGridThreads, 0);
     if (err != cudaSuccess) return err;
-    const GridGeom G{H, W, gx, gy, gz, sigma_s, sigma_r, lo, field};
-    const int nsp = (gx - 2 * kPad + 1) * (gy - 2 * kPad + 1);
-    k6_splat<<<stream_blocks((size_t)nsp, num_sms), kGridThreads, 0, s>>>(f, ga, G);
-    const int nb = stream_blocks(cells, num_sms);
-    k6_blur<<<nb, kGridThreads, 0, s>>>(ga, gb, gx, gy, gz, 0);
-    k6_blur<<<nb, kGridThreads, 0, s>>>(gb, ga, gx, gy, gz, 1);
-    k6_blur<<<nb, kGridThreads, 0, s>>>(ga, gb, gx, gy, gz, 2);
-    k6_slice<<<stream_blocks((size_t)H * W, num_sms), kGridThreads, 0, s>>>(f, gb, e, G);
-    return cudaGetLastError();
+    const dim3 grid((unsigned)(num_sms * std::max(1, std::min(occ, 4))));
+    void* args[] = {(void*)&P, (void*)&max_cells};
+    return cudaLaunchCooperativeKernel((const void*)k6_grid_field, grid, dim3(kGridThreads), args,
+                                       0, s);
 }
 
 }  // namespace blfls

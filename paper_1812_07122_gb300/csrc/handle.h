@@ -36,13 +36,12 @@ struct blfls_handle {
     size_t layer_cap = 0;
     float* gtmp = nullptr;   // blfls_gaussian: one plane after the row pass
     size_t gtmp_cap = 0;
-    // blfls_smooth_grid: the two grid buffers, range keys on the device and their host copy
+    // blfls_smooth_grid: the two grid buffers (one chunk of range levels each) and the range keys
     float2* grid_a = nullptr;
     float2* grid_b = nullptr;
     size_t grid_cap = 0;     // cells per buffer
     int* grid_keys = nullptr;
     size_t grid_keys_cap = 0;
-    int* grid_keys_host = nullptr;   // pinned, 4 * BLFLS_MAX_CHANNELS
     float4* kap_dev = nullptr;       // blfls_smooth_normalized: range constants per channel
     size_t kap_cap = 0;
     float* nc_scratch = nullptr;     // blfls_smooth_nc: gradients, transforms, two buffers

@@ -180,20 +180,19 @@ cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int 
                             int R, cudaStream_t s, int num_sms);
 
 // Bilateral-grid BLF (grid.cu).  launch_grid_minmax: keys[4c + 2 field + {0, 1}] receive the
-// order-preserving keys of min / max of field (0: x, 1: y) of channel c (decode with
-// grid_key_to_float).  launch_grid_residual: e = BLF_grid(g_field) - g_field for one channel;
-// ga, gb hold gx * gy * gz float2 each.
+// order-preserving keys of min / max of field (0: x, 1: y) of channel c.  launch_grid_field:
+// e = BLF_grid(g_field) - g_field for one channel, the range levels from keys (this field's pair)
+// on the device; ga, gb hold (zc + 2) gx gy float2 each (grid_spatial_dims, grid_chunk_levels).
 cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys, cudaStream_t s,
                                int num_sms);
-float grid_key_to_float(int key);
 // Normalised gradients: per channel, the range constants (kx, ky, 1/kx, 1/ky) of the two fields
 // from their range keys (launch_grid_minmax), sigma_r scaled by each field's range, on the device.
 cudaError_t launch_range_kappa(const int* keys, int C, float sigma_r, float4* kap, cudaStream_t s);
-void grid_dims(int H, int W, float lo, float hi, float sigma_s, float sigma_r, int* gx, int* gy,
-               int* gz);
-cudaError_t launch_grid_residual(const float* f, float* e, int field, int H, int W, float sigma_s,
-                                 float sigma_r, float lo, int gx, int gy, int gz, float2* ga,
-                                 float2* gb, cudaStream_t s, int num_sms);
+void grid_spatial_dims(int H, int W, float sigma_s, int* gx, int* gy);
+int grid_chunk_levels(float sigma_r, int gx, int gy);
+cudaError_t launch_grid_field(const float* f, float* e, int field, int H, int W, float sigma_s,
+                              float sigma_r, const int* keys, int gx, int gy, int zc, float2* ga,
+                              float2* gb, cudaStream_t s, int num_sms);
 
 // NC-LS (nc.cu): ex, ey = NC(g) - g for one channel f, n_iter box iterations; `scratch` holds
 // nc_scratch_floats(H, W) floats.

@@ -131,7 +131,45 @@ def test_grid_rejects_invalid_arguments(h):
     f = to_dev(_img(32, 32, 1))
     out = torch.empty_like(f)
     for ss, sr, lam in ((0.25, 0.1, 20.0), (math.inf, 0.1, 20.0), (2.0, 0.0, 20.0),
-                        (2.0, 0.1, -1.0), (2.0, 1e-9, 20.0)):
+                        (2.0, 0.1, -1.0)):
         with pytest.raises(blfls.BlflsError) as ei:
             blfls.blfls_smooth_grid(h, f, out, 32, 32, 1, lam, ss, sr, 1, stream())
         assert ei.value.code == blfls.BLFLS_EINVAL
+
+
+def test_grid_wide_range_in_many_chunks(h):
+    """A field far wider than the range the grid buffers are sized for (an image in [0, 40],
+    sigma_r = 0.5: about 160 range cells in chunks of 9 levels) is filtered chunk by chunk on the
+    device and still matches the FP64 oracle."""
+    f = (40.0 * _img(48, 64, 1, seed=11)).astype(np.float32)
+    check_grid_pass(h, f, 20.0, 3.0, 0.5)
+
+
+def test_grid_range_beyond_the_cell_cap_gives_nan(h):
+    """A range of more than BLFLS_GRID_MAX_RANGE_CELLS cells of sigma_r cannot be gridded: the
+    call (which never reads the range back) succeeds and the channel's output is NaN; a channel
+    within the cap beside it is unaffected."""
+    f = _img(32, 32, 2, seed=4)
+    f[1] *= 1e-6                                    # channel 1: range about 2e-6 -> 2 cells
+    got = _grid(h, f, 20.0, 2.0, 1e-9)
+    assert np.isnan(got[0]).all()
+    np.testing.assert_array_equal(got[1], _grid(h, f[1:], 20.0, 2.0, 1e-9)[0])
+    assert np.isfinite(got[1]).all()
+
+
+def test_grid_does_not_wait_for_the_stream(h):
+    """The ranges stay on the device: the call returns while the stream is still busy, and the
+    result is the same as a call on an idle stream."""
+    f = _img(96, 128, 3, seed=6)
+    want = _grid(h, f, 20.0, 3.0, 0.1, 2)
+    x = to_dev(f)
+    out = torch.empty_like(x)
+    torch.cuda.synchronize(DEV)
+    s = stream()
+    torch.cuda._sleep(200_000_000)                        # ~0.1 s of spinning on the stream
+    blfls.blfls_smooth_grid(h, x, out, 96, 128, 3, 20.0, 3.0, 0.1, 2, s)
+    done = torch.cuda.Event()
+    done.record(s)
+    assert not done.query(), "the call waited for the stream"
+    torch.cuda.synchronize(DEV)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
