@@ -847,6 +847,21 @@ __device__ __forceinline__ int ct_frequency(unsigned p)
     return ct_frequency_digits<P>(p, std::make_integer_sequence<int, P::nst>{});
 }
 
+// Work position of frequency k after the forward transform of plan P (the inverse of
+// ct_frequency; the same as the plan's perm table).
+template <class P, int... S>
+__device__ __forceinline__ unsigned ct_position_digits(unsigned k, std::integer_sequence<int, S...>)
+{
+    unsigned p = 0;
+    ((p += (k % (unsigned)P::radix[S]) * (unsigned)P::span(S), k /= (unsigned)P::radix[S]), ...);
+    return p;
+}
+template <class P>
+__device__ __forceinline__ unsigned ct_position(unsigned k)
+{
+    return ct_position_digits<P>(k, std::make_integer_sequence<int, P::nst>{});
+}
+
 // Stage s of plan P as a CtStage (NC interleaved columns).
 template <class P, int S, int NC, int PADS>
 using CtStageOf = CtStage<P::radix[S], P::span(S), P::L, NC, PADS>;

@@ -564,29 +564,36 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
     int p0, p1;
     band(npairs, p0, p1);
     if (p0 >= p1) return;
+    // Staging slots: e_x rows y0, y1, e_y row y0, and two e_y slots that alternate: pair i of the
+    // band (i = p - p0) stages its e_y row y1 in slot i mod 2, which is the row y0 - 1 the next
+    // pair needs, so each e_y row is copied once (the band's first pair also copies its y0 - 1).
+    float* const eyslot[2] = {st + 3 * Wp, st + 4 * Wp};
     auto issue = [&](int p) {
+        const int i = p - p0;
         const int y0 = 2 * p, y1 = y0 + 1;
-        const int ym = (y0 == 0) ? H - 1 : y0 - 1;
         stage_floats(st, ex + (size_t)y0 * W, W, vec);
-        stage_floats(st + 2 * Wp, ey + (size_t)ym * W, W, vec);
-        stage_floats(st + 3 * Wp, ey + (size_t)y0 * W, W, vec);
+        stage_floats(st + 2 * Wp, ey + (size_t)y0 * W, W, vec);
+        if (i == 0) {
+            const int ym = (y0 == 0) ? H - 1 : y0 - 1;
+            stage_floats(eyslot[1], ey + (size_t)ym * W, W, vec);
+        }
         if (y1 < H) {
             stage_floats(st + Wp, ex + (size_t)y1 * W, W, vec);
-            stage_floats(st + 4 * Wp, ey + (size_t)y1 * W, W, vec);
+            stage_floats(eyslot[i & 1], ey + (size_t)y1 * W, W, vec);
         }
         cp_commit();
     };
     const float* ex0 = st;
     const float* ex1 = st + Wp;
-    const float* eym = st + 2 * Wp;
-    const float* ey0 = st + 3 * Wp;
-    const float* ey1 = st + 4 * Wp;
+    const float* ey0 = st + 2 * Wp;
     issue(p0);
     for (int p = p0; p < p1; ++p) {
         cp_wait<0>();
         __syncthreads();
         const int y0 = 2 * p, y1 = y0 + 1;
         const bool has1 = y1 < H;
+        const float* eym = eyslot[(p - p0 + 1) & 1];
+        const float* ey1 = eyslot[(p - p0) & 1];
         for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
@@ -617,8 +624,8 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
 #pragma unroll 4
         for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
             const int kn = (k == 0) ? 0 : W - k;
-            const float2 zk = data[row_pos(rp, __ldg(rp.perm + k))];
-            const float2 zn = data[row_pos(rp, __ldg(rp.perm + kn))];
+            const float2 zk = data[S0::offset(ct_position<P>((unsigned)k), 0)];
+            const float2 zn = data[S0::offset(ct_position<P>((unsigned)kn), 0)];
             // A = (Z_k + conj Z_{W-k}) / 2,  B = (Z_k - conj Z_{W-k}) / (2i)
             s0[k] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
             if (has1) s1[k] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
