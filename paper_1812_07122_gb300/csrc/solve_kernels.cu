@@ -781,9 +781,13 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k4_rows_fused(const float2*
             SL::locate(b, nat, j, col);
             if (!SL::in_buffer(SL::offset(nat, col))) continue;
             float2 v[RL], o[RL];
+            // the last stage has span 1: position nat + q holds frequency k(nat) + q R_0..R_{NL-1}
+            const int k0 = ct_frequency<P>(nat);
+            static_assert(P::span(NL) == 1, "the last stage has span 1");
+            constexpr int wl = P::L / RL;
 #pragma unroll
             for (int q = 0; q < RL; ++q) {
-                const int k = ct_frequency<P>(nat + q);
+                const int k = k0 + q * wl;
                 const bool upper = k > W / 2;
                 const int kk = upper ? W - k : k;
                 float2 a = ss[kk];
