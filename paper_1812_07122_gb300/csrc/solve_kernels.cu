@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(512) k4_rows_inverse(
 constexpr int kStagedThreads = 256;
 
 __host__ __device__ __forceinline__ size_t row_floats(int W) { return (size_t)((W + 3) & ~3); }
-// K2: [5][Wp] floats (e_x rows y0, y1; e_y rows y0-1, y0, y1), then the FFT buffer.
+// K2: [5][Wp] floats (e_x rows y0, y1 and e_y rows y0-1, y0, y1), then the FFT buffer.
 __host__ __device__ __forceinline__ size_t k2s_stage_bytes(int W) { return sizeof(float) * 5 * row_floats(W); }
 __host__ __device__ __forceinline__ size_t k2s_smem(int W, const FftPlanDev& rp)
 {
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
     // Staging slots: e_x rows y0, y1, e_y row y0, and two e_y slots that alternate: pair i of the
     // band (i = p - p0) stages its e_y row y1 in slot i mod 2, which is the row y0 - 1 the next
     // pair needs, so each e_y row is copied once (the band's first pair also copies its y0 - 1).
-    float* const eyslot[2] = {st + 3 * Wp, st + 4 * Wp};
+    auto eyslot = [&](int k) { return st + (3 + (k & 1)) * Wp; };
     auto issue = [&](int p) {
         const int i = p - p0;
         const int y0 = 2 * p, y1 = y0 + 1;
@@ -575,11 +575,11 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
         stage_floats(st + 2 * Wp, ey + (size_t)y0 * W, W, vec);
         if (i == 0) {
             const int ym = (y0 == 0) ? H - 1 : y0 - 1;
-            stage_floats(eyslot[1], ey + (size_t)ym * W, W, vec);
+            stage_floats(eyslot(1), ey + (size_t)ym * W, W, vec);
         }
         if (y1 < H) {
             stage_floats(st + Wp, ex + (size_t)y1 * W, W, vec);
-            stage_floats(eyslot[i & 1], ey + (size_t)y1 * W, W, vec);
+            stage_floats(eyslot(i), ey + (size_t)y1 * W, W, vec);
         }
         cp_commit();
     };
@@ -592,8 +592,8 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k2_rows_fused(const float* 
         __syncthreads();
         const int y0 = 2 * p, y1 = y0 + 1;
         const bool has1 = y1 < H;
-        const float* eym = eyslot[(p - p0 + 1) & 1];
-        const float* ey1 = eyslot[(p - p0) & 1];
+        const float* eym = eyslot(p - p0 + 1);
+        const float* ey1 = eyslot(p - p0);
         for (unsigned b = threadIdx.x; b < S0::total; b += blockDim.x) {
             unsigned nat, j, col;
             S0::locate(b, nat, j, col);
