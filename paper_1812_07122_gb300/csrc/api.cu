@@ -837,8 +837,10 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
     }
     const FftPlanDev *rp = nullptr, *cp = nullptr;
     if ((rc = prepare(h, H, W, 0, false, true, &rp, &cp)) != BLFLS_OK) return rc;
-    if ((rc = grow(h, h->grid_keys, h->grid_keys_cap, 4 * (size_t)BLFLS_MAX_CHANNELS, "grid keys")) != BLFLS_OK)
+    // range keys (4 ints per channel), then the levels of every field (one int4 each)
+    if ((rc = grow(h, h->grid_keys, h->grid_keys_cap, 12 * (size_t)BLFLS_MAX_CHANNELS, "grid keys")) != BLFLS_OK)
         return rc;
+    int4* lev = reinterpret_cast<int4*>(h->grid_keys + 4 * BLFLS_MAX_CHANNELS);
     // the buffers hold one chunk of range levels; a wider range takes more chunks on the device
     int gx = 0, gy = 0;
     grid_spatial_dims(H, W, sigma_s, &gx, &gy);
@@ -851,12 +853,13 @@ int blfls_smooth_grid(blfls_handle* h, const float* img, float* out, int H, int 
     for (int it = 0; it < iters; ++it) {
         const float* src = (it == 0) ? img : out;
         cudaError_t e = launch_grid_minmax(src, H, W, C, h->grid_keys, s, h->num_sms);
+        if (e == cudaSuccess) e = launch_grid_levels(h->grid_keys, C, sigma_r, zc, lev, s);
         if (e != cudaSuccess) return cuda_fail(e, "grid range kernel launch");
         for (int c = 0; c < C; ++c) {
             const float* fc = src + c * plane;
             for (int field = 0; field < 2; ++field) {
                 e = launch_grid_field(fc, field == 0 ? h->ex : h->ey, field, H, W, sigma_s,
-                                      sigma_r, h->grid_keys + 4 * c + 2 * field, gx, gy, zc,
+                                      sigma_r, lev + 2 * c + field, gx, gy, zc,
                                       h->grid_a, h->grid_b, s, h->num_sms);
                 if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
             }

@@ -8,12 +8,14 @@
 // (floor((W-1)/s_s) + 1 + 2P) cells, z-major:
 //   k6_minmax      min and max of both fields of every channel (order-preserving integer keys, so
 //                  the atomics are exact and the result does not depend on their order);
-//   k6_grid_field  one cooperative launch per field: Gz from the keys on the device, then, chunk
-//                  by chunk of range levels: splat (one thread per spatial cell walks the pixels
-//                  whose nearest cell it is and adds (g, 1) to the range level of each, in a fixed
-//                  order: deterministic, no atomics), the 3-tap blur (e^-1/2, 1, e^-1/2) along x,
-//                  y, then z (zero outside), and the trilinear slice at (z, y / s_s + P,
-//                  x / s_s + P): e = sum / count - g.
+//   k6_*0         the first chunk of range levels of one field, one launch per phase, the levels
+//                 from the range keys on the device: clear; splat (one thread per spatial cell
+//                 walks the pixels whose nearest cell it is and adds (g, 1) to the range level of
+//                 each, in a fixed order: deterministic, no atomics); the 3-tap blur (e^-1/2, 1,
+//                 e^-1/2) along x, y, then z (zero outside); the trilinear slice at
+//                 (z, y / s_s + P, x / s_s + P): e = sum / count - g;
+//   k6_chunks     the further chunks of a wider field (one cooperative launch, grid-wide
+//                 barriers between the phases; it returns at once for one chunk).
 // The range is never read back to the host: the buffers hold a chunk of levels whose size the
 // host fixes, and a wider range takes more chunks.
 // Cell indices are floor(t + 1/2) of the real t: FP32 decides away from rounding boundaries, FP64
@@ -101,7 +103,7 @@ __device__ __forceinline__ float key_to_float(int key)
 struct GridChunk {
     const float* f;
     float* e;
-    const int* keys;    // order-preserving min / max keys of this field (launch_grid_minmax)
+    const int4* lev;    // this field's levels (k6_levels): lo (bits), gz, chunks, ok
     float2* ga;
     float2* gb;         // (zc + 2) x gy x gx cells each
     int H, W, gx, gy, zc, field;
@@ -155,32 +157,83 @@ __device__ __forceinline__ void grid_splat(const GridChunk& P, float lo, int gz,
     }
 }
 
-// out = in + e (in[-stride] + in[+stride]) along x (axis 0) or y (axis 1) of every level, or
-// along z (axis 2) for the chunk's interior levels; zero outside the whole grid.
+// The range levels of a field's grid from its range keys, as the FP64 definition
+// floor((max - min) / s_r) + 1 + 2P, and the chunks that cover them (chunk k: zb = k (zc - 1)).
+// A range of more than max_cells cells of s_r, or a NaN range, cannot be gridded (ok = 0).
+// One thread per field (k6_levels); the phase kernels read the result.
+struct GridLevels {
+    float lo;
+    int gz, nchunks;
+    bool ok;
+};
+__global__ void k6_levels(const int* __restrict__ keys, int nfields, float sigma_r, int zc,
+                          int max_cells, int4* __restrict__ lev)
+{
+    const int q = threadIdx.x;
+    if (q >= nfields) return;
+    const float lo = key_to_float(keys[2 * q]);
+    const float hi = key_to_float(keys[2 * q + 1]);
+    const double span = floor(((double)hi - (double)lo) / (double)sigma_r);
+    const bool ok = span >= 0.0 && span <= (double)max_cells;
+    const int gz = ok ? (int)span + 1 + 2 * kPad : 0;
+    const int nchunks = ok ? (gz - 1 + zc - 2) / (zc - 1) : 0;   // chunks of z0 in [0, gz - 2]
+    lev[q] = make_int4(__float_as_int(lo), gz, nchunks, ok ? 1 : 0);
+}
+__device__ __forceinline__ GridLevels grid_levels(const GridChunk& P)
+{
+    const int4 v = __ldg(P.lev);
+    return GridLevels{__int_as_float(v.x), v.y, v.z, v.w != 0};
+}
+
+// Buffer levels chunk zb fills: l in [l0, l1), global z = zb + l - 1 inside the grid's [0, gz)
+// (l0 = 0 below the first chunk's bottom level, l1 up to zc + 2 over its top one: the levels just
+// outside a chunk are its z blur's neighbours; levels outside the grid are never read).
+struct ChunkLevels {
+    int l0, l1;
+};
+__device__ __forceinline__ ChunkLevels chunk_levels(const GridChunk& P, int gz, int zb)
+{
+    return ChunkLevels{zb == 0 ? 1 : 0, min(P.zc + 2, gz - zb + 1)};
+}
+
+// A chunk holds fewer than 2^32 cells (its buffers are bounded by BLFLS_GRID_MAX_BYTES), so the
+// cell loops use 32-bit indices.
+__device__ __forceinline__ void grid_clear(const GridChunk& P, ChunkLevels cl, unsigned tid,
+                                           unsigned nthreads)
+{
+    const unsigned slab = (unsigned)P.gx * P.gy;
+    const unsigned first = slab * (unsigned)cl.l0, n = slab * (unsigned)(cl.l1 - cl.l0);
+    for (unsigned k = tid; k < n; k += nthreads) P.ga[first + k] = make_float2(0.f, 0.f);
+}
+
+// out = in + e (in[-stride] + in[+stride]) along x (axis 0) or y (axis 1) of the chunk's levels,
+// or along z (axis 2) for its interior levels inside the grid; zero outside the whole grid.
 __device__ __forceinline__ void grid_blur(const float2* __restrict__ in, float2* __restrict__ out,
-                                          const GridChunk& P, int gz, int zb, int axis,
-                                          size_t tid, size_t nthreads)
+                                          const GridChunk& P, int gz, int zb, ChunkLevels cl,
+                                          int axis, unsigned tid, unsigned nthreads)
 {
     const float e = 0.60653065971263342f;   // exp(-1/2)
-    const size_t slab = (size_t)P.gx * P.gy;
-    const size_t first = axis == 2 ? slab : 0;
-    const size_t n = axis == 2 ? slab * (size_t)P.zc : slab * (size_t)(P.zc + 2);
-    const size_t stride = axis == 0 ? 1 : axis == 1 ? (size_t)P.gx : slab;
-    for (size_t k = tid; k < n; k += nthreads) {
-        const size_t i = first + k;
+    const unsigned gx = (unsigned)P.gx, gy = (unsigned)P.gy;
+    const unsigned slab = gx * gy;
+    const int la = axis == 2 ? 1 : cl.l0;
+    const int lb = axis == 2 ? min(P.zc + 1, gz - zb + 1) : cl.l1;
+    const unsigned first = slab * (unsigned)la;
+    const unsigned n = lb > la ? slab * (unsigned)(lb - la) : 0u;
+    const unsigned stride = axis == 0 ? 1u : axis == 1 ? gx : slab;
+    for (unsigned k = tid; k < n; k += nthreads) {
+        const unsigned i = first + k;
         int pos, len;
         if (axis == 0) {
-            pos = (int)(i % (size_t)P.gx);
+            pos = (int)(i % gx);
             len = P.gx;
         } else if (axis == 1) {
-            pos = (int)((i / (size_t)P.gx) % (size_t)P.gy);
+            pos = (int)((i / gx) % gy);
             len = P.gy;
         } else {
             pos = (int)(i / slab) - 1 + zb;   // global level
             len = gz;
-            if (pos >= gz) continue;          // beyond the grid: never sliced
         }
-        float2 a = in[i];
+        const float2 a = in[i];
         float2 s = make_float2(0.f, 0.f);
         if (pos > 0) { const float2 b = in[i - stride]; s.x += b.x; s.y += b.y; }
         if (pos + 1 < len) { const float2 b = in[i + stride]; s.x += b.x; s.y += b.y; }
@@ -222,42 +275,64 @@ __device__ __forceinline__ void grid_slice(const GridChunk& P, float lo, int gz,
     }
 }
 
-// The whole grid filter of one field in one cooperative launch: the range levels follow from the
-// field's range keys on the device (no read-back), then for each chunk: clear, splat, blur x, y, z,
-// slice, with a grid-wide barrier between the phases.  Every block takes the same branches, so
-// every block reaches every barrier.  A range of more than max_cells cells of sigma_r (or a NaN
-// range) gives NaN residuals for the field.
-__global__ void __launch_bounds__(kGridThreads) k6_grid_field(GridChunk P, int max_cells)
+__device__ __forceinline__ unsigned gtid() { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ unsigned gthreads() { return gridDim.x * blockDim.x; }
+
+// The first chunk (the only one for a field of range up to 2 and the chunk size the host picks)
+// in one launch per phase: each kernel reads the levels from the range keys.
+__global__ void __launch_bounds__(kGridThreads) k6_clear0(GridChunk P)
 {
-    cg::grid_group grid = cg::this_grid();
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nthreads = (size_t)gridDim.x * blockDim.x;
-    const float lo = key_to_float(P.keys[0]);
-    const float hi = key_to_float(P.keys[1]);
-    // the number of range cells, as the FP64 definition floor((max - min) / s_r) + 1 + 2P
-    const double span = floor(((double)hi - (double)lo) / (double)P.sr);
-    if (!(span >= 0.0 && span <= (double)max_cells)) {
+    const GridLevels G = grid_levels(P);
+    if (G.ok) grid_clear(P, chunk_levels(P, G.gz, 0), gtid(), gthreads());
+}
+__global__ void __launch_bounds__(kGridThreads) k6_splat0(GridChunk P)
+{
+    const GridLevels G = grid_levels(P);
+    if (G.ok) grid_splat(P, G.lo, G.gz, 0, gtid(), gthreads());
+}
+__global__ void __launch_bounds__(kGridThreads) k6_blur0(GridChunk P, int axis)
+{
+    const GridLevels G = grid_levels(P);
+    if (!G.ok) return;
+    const float2* in = axis == 1 ? P.gb : P.ga;
+    float2* out = axis == 1 ? P.ga : P.gb;
+    grid_blur(in, out, P, G.gz, 0, chunk_levels(P, G.gz, 0), axis, gtid(), gthreads());
+}
+__global__ void __launch_bounds__(kGridThreads) k6_slice0(GridChunk P)
+{
+    const GridLevels G = grid_levels(P);
+    if (!G.ok) {
         const size_t plane = (size_t)P.H * P.W;
-        for (size_t i = tid; i < plane; i += nthreads) P.e[i] = __int_as_float(0x7fc00000);
+        for (size_t i = gtid(); i < plane; i += gthreads()) P.e[i] = __int_as_float(0x7fc00000);
         return;
     }
-    const int gz = (int)span + 1 + 2 * kPad;
-    const int nchunks = (gz - 1 + P.zc - 2) / (P.zc - 1);   // chunks of z0 in [0, gz - 2]
-    const size_t cells = (size_t)P.gx * P.gy * (size_t)(P.zc + 2);
-    for (int k = 0; k < nchunks; ++k) {
+    grid_slice(P, G.lo, G.gz, 0, gtid(), gthreads());
+}
+
+// The remaining chunks of a wider field, in one cooperative launch with a grid-wide barrier
+// between the phases (returns at once when the first chunk covered the field).  Every block
+// takes the same branches, so every block reaches every barrier.
+__global__ void __launch_bounds__(kGridThreads) k6_chunks(GridChunk P)
+{
+    const GridLevels G = grid_levels(P);
+    if (G.nchunks <= 1) return;
+    cg::grid_group grid = cg::this_grid();
+    const unsigned tid = gtid(), nthreads = gthreads();
+    for (int k = 1; k < G.nchunks; ++k) {
         const int zb = k * (P.zc - 1);
-        for (size_t i = tid; i < cells; i += nthreads) P.ga[i] = make_float2(0.f, 0.f);
+        const ChunkLevels cl = chunk_levels(P, G.gz, zb);
+        grid.sync();   // the previous chunk's slice has read the buffers
+        grid_clear(P, cl, tid, nthreads);
         grid.sync();
-        grid_splat(P, lo, gz, zb, tid, nthreads);
+        grid_splat(P, G.lo, G.gz, zb, tid, nthreads);
         grid.sync();
-        grid_blur(P.ga, P.gb, P, gz, zb, 0, tid, nthreads);
+        grid_blur(P.ga, P.gb, P, G.gz, zb, cl, 0, tid, nthreads);
         grid.sync();
-        grid_blur(P.gb, P.ga, P, gz, zb, 1, tid, nthreads);
+        grid_blur(P.gb, P.ga, P, G.gz, zb, cl, 1, tid, nthreads);
         grid.sync();
-        grid_blur(P.ga, P.gb, P, gz, zb, 2, tid, nthreads);
+        grid_blur(P.ga, P.gb, P, G.gz, zb, cl, 2, tid, nthreads);
         grid.sync();
-        grid_slice(P, lo, gz, zb, tid, nthreads);
-        grid.sync();
+        grid_slice(P, G.lo, G.gz, zb, tid, nthreads);
     }
 }
 
@@ -333,20 +408,32 @@ int grid_chunk_levels(float sigma_r, int gx, int gy)
     return (int)std::max(8.0, std::min(want, budget));
 }
 
+cudaError_t launch_grid_levels(const int* keys, int C, float sigma_r, int zc, int4* lev,
+                               cudaStream_t s)
+{
+    k6_levels<<<1, 2 * BLFLS_MAX_CHANNELS, 0, s>>>(keys, 2 * C, sigma_r, zc,
+                                                    BLFLS_GRID_MAX_RANGE_CELLS, lev);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_grid_field(const float* f, float* e, int field, int H, int W, float sigma_s,
-                              float sigma_r, const int* keys, int gx, int gy, int zc, float2* ga,
+                              float sigma_r, const int4* lev, int gx, int gy, int zc, float2* ga,
                               float2* gb, cudaStream_t s, int num_sms)
 {
-    const GridChunk P{f, e, keys, ga, gb, H, W, gx, gy, zc, field, sigma_s, sigma_r};
-    int max_cells = BLFLS_GRID_MAX_RANGE_CELLS;
-    int occ = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_grid_field,
-                                                                     kGridThreads, 0);
+    const GridChunk P{f, e, lev, ga, gb, H, W, gx, gy, zc, field, sigma_s, sigma_r};
+    const size_t cells = (size_t)gx * gy * (size_t)(zc + 2);
+    const int nsp = (gx - 2 * kPad + 1) * (gy - 2 * kPad + 1);
+    const int nb = stream_blocks(cells, num_sms);
+    k6_clear0<<<nb, kGridThreads, 0, s>>>(P);
+    k6_splat0<<<stream_blocks((size_t)nsp, num_sms), kGridThreads, 0, s>>>(P);
+    for (int axis = 0; axis < 3; ++axis) k6_blur0<<<nb, kGridThreads, 0, s>>>(P, axis);
+    k6_slice0<<<stream_blocks((size_t)H * W, num_sms), kGridThreads, 0, s>>>(P);
+    const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const dim3 grid((unsigned)(num_sms * std::max(1, std::min(occ, 4))));
-    void* args[] = {(void*)&P, (void*)&max_cells};
-    return cudaLaunchCooperativeKernel((const void*)k6_grid_field, grid, dim3(kGridThreads), args,
-                                       0, s);
+    // one block per SM: the launch returns at once in the usual case of a single chunk
+    void* args[] = {(void*)&P};
+    return cudaLaunchCooperativeKernel((const void*)k6_chunks, dim3((unsigned)num_sms),
+                                       dim3(kGridThreads), args, 0, s);
 }
 
 }  // namespace blfls

@@ -180,9 +180,11 @@ cudaError_t launch_gaussian(const float* in, float* tmp, float* out, int H, int 
                             int R, cudaStream_t s, int num_sms);
 
 // Bilateral-grid BLF (grid.cu).  launch_grid_minmax: keys[4c + 2 field + {0, 1}] receive the
-// order-preserving keys of min / max of field (0: x, 1: y) of channel c.  launch_grid_field:
-// e = BLF_grid(g_field) - g_field for one channel, the range levels from keys (this field's pair)
-// on the device; ga, gb hold (zc + 2) gx gy float2 each (grid_spatial_dims, grid_chunk_levels).
+// order-preserving keys of min / max of field (0: x, 1: y) of channel c.  launch_grid_levels:
+// lev[2c + field] = the range levels of that field's grid (zc levels per chunk).
+// launch_grid_field: e = BLF_grid(g_field) - g_field for one channel from its levels (lev points
+// at this field's entry); ga, gb hold (zc + 2) gx gy float2 each (grid_spatial_dims,
+// grid_chunk_levels).
 cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys, cudaStream_t s,
                                int num_sms);
 // Normalised gradients: per channel, the range constants (kx, ky, 1/kx, 1/ky) of the two fields
@@ -190,8 +192,10 @@ cudaError_t launch_grid_minmax(const float* img, int H, int W, int C, int* keys,
 cudaError_t launch_range_kappa(const int* keys, int C, float sigma_r, float4* kap, cudaStream_t s);
 void grid_spatial_dims(int H, int W, float sigma_s, int* gx, int* gy);
 int grid_chunk_levels(float sigma_r, int gx, int gy);
+cudaError_t launch_grid_levels(const int* keys, int C, float sigma_r, int zc, int4* lev,
+                               cudaStream_t s);
 cudaError_t launch_grid_field(const float* f, float* e, int field, int H, int W, float sigma_s,
-                              float sigma_r, const int* keys, int gx, int gy, int zc, float2* ga,
+                              float sigma_r, const int4* lev, int gx, int gy, int zc, float2* ga,
                               float2* gb, cudaStream_t s, int num_sms);
 
 // NC-LS (nc.cu): ex, ey = NC(g) - g for one channel f, n_iter box iterations; `scratch` holds
