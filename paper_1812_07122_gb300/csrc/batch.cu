@@ -173,7 +173,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
             const FftPlanDev* rp;
             const FftPlanDev* cp;
             float kappa, inv_kappa, cs;
-            int lgc, tiles_x, tiles_y, tile_h;
+            int lgc, rec, tiles_x, tiles_y, tile_h;
             size_t o_ex, o_ey, o_spec;
         };
         std::vector<Info> info(batched.size());
@@ -191,6 +191,9 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
             // memory, so cap every job's block at kBatchColBytes: one long (e.g. Bluestein)
             // column set must not cut the occupancy of every other job's items.
             while (I.lgc > 0 && (sizeof(float2) * (size_t)I.cp->L << I.lgc) > kBatchColBytes) --I.lgc;
+            // a column length that needs Bluestein is solved by the recursion, 32 columns a block
+            I.rec = I.cp->bluestein && j.lambda <= kRecLamMax ? 1 : 0;
+            if (I.rec) I.lgc = 5;
             I.tile_h = blf_tile_height(tuned_tile_h(h, j.radius, j.prec));
             blf_tiles(j.H, j.W, I.tile_h, &I.tiles_x, &I.tiles_y);
             const size_t planes = (size_t)j.C * j.H * j.W;
@@ -234,6 +237,7 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
                 J.lam = j.lambda;
                 J.scale = 1.0f / ((float)j.H * (float)j.W);
                 J.lgc = I.lgc;
+                J.rec = I.rec;
                 J.tiles_x = I.tiles_x;
                 J.tiles_y = I.tiles_y;
                 J.tile_h = I.tile_h;
@@ -257,7 +261,8 @@ int run_batch(blfls_handle* h, const blfls_job* jobs, int n, cudaStream_t user)
                 P.total_cols += j.C * ((j.W / 2 + 1 + (1 << I.lgc) - 1) >> I.lgc);
                 P.smem_rows = std::max(P.smem_rows, sizeof(float2) * (size_t)row_buf_elems(*I.rp));
                 P.max_w = std::max(P.max_w, j.W);
-                P.smem_cols = std::max(P.smem_cols, (sizeof(float2) * (size_t)I.cp->L) << I.lgc);
+                P.smem_cols = std::max(P.smem_cols, I.rec ? solve_rec_smem(j.H)
+                                                           : (sizeof(float2) * (size_t)I.cp->L) << I.lgc);
             }
             max_groups = std::max(max_groups, (int)P.groups.size());
             P.o_table = blob;

@@ -74,6 +74,11 @@ void set_last_error(const std::string& msg);
 // ---------------------------------------------------------------------------------------------
 // Batched form: one entry per job of the device job table of one pass.
 // ---------------------------------------------------------------------------------------------
+// K3 solves a column length without a mixed-radix plan (one that needs Bluestein) by the cyclic
+// recursion its divide amounts to, in segments of kRecSeg rows, while lambda <= kRecLamMax.
+constexpr int kRecSeg = 32;
+constexpr float kRecLamMax = 1.0e4f;
+
 struct BatchJob {
     const float* src;   // this pass's input  [C][H][W]
     float* dst;         // this pass's output [C][H][W]
@@ -84,6 +89,7 @@ struct BatchJob {
     float kappa, inv_kappa, cs;   // bilateral constants (see launch_blf_residual)
     float lam, scale;             // solve: lambda and 1/(H W)
     int lgc;                      // log2 of the column block of K3
+    int rec;                      // K3 by recursion (lgc = 5), see kRecLamMax
     int tiles_x, tiles_y;         // K1 tiling
     int tile_h;                   // K1 tile height (rows)
     FftPlanDev rp, cp;            // row (length W) and column (length H) plans
@@ -142,6 +148,8 @@ struct SolveParams {
     int col_block;   // columns per CTA in K3 (1..16; 0: the column driver's own choice)
 };
 
+// Shared memory of the recursion K3 (kRecSeg) on a 32-column block of columns of length H.
+size_t solve_rec_smem(int H);
 // The K3 column block a solve launch takes for a requested col_block (0: the driver's own
 // choice) with column plan cp on an image W wide.
 int solve_effective_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms);

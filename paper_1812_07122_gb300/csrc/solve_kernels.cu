@@ -145,6 +145,165 @@ __device__ __forceinline__ void k2_item(const float* __restrict__ ex, const floa
             data);
 }
 
+// ---- column solve by recursion (column lengths without a mixed-radix plan) ----------------------
+// Along a column of fixed x frequency kx, Eq. 8's column DFT, divide by 1 + lam (sx + sy) and
+// inverse DFT is the solve of the cyclic tridiagonal system
+//     (1 + lam sx) Z - lam (Z[n+1] - 2 Z[n] + Z[n-1]) = lam R        (periodic in n),
+// because the DFT diagonalises the periodic second difference with eigenvalues sy.  The operator
+// factors as (lam / r) (1 - r S)(1 - r S^-1), S the cyclic shift and r in [0, 1) the smaller root
+// of lam r^2 - d r + lam = 0, d = 1 + lam sx + 2 lam, so Z = r (1 - r S^-1)^-1 (1 - r S)^-1 R
+// (times the H / (HW) the unnormalised transforms would apply): a causal and an anticausal
+// first-order recursion, each cyclic.  Every column is split into segments of kRecSeg rows: each
+// segment runs its recursion from zero, the segments' carries are chained per column (the cyclic
+// start value from the geometric sum over the whole column), and each segment adds its carry's
+// decay.  The segments depend only on H, so a column's result does not depend on how columns
+// are grouped.  The recursion amplifies rounding by about 1 / (1 - r), largest at kx = 0; it is
+// used while lam <= kRecLamMax (1 / (1 - r) below about 100), Bluestein column transforms above.
+
+// r, r^kRecSeg, r^(rows of the last segment) and 1 / (1 - r^H) of a column
+struct RecCoef {
+    float r, rseg, rlast, icyc;
+};
+__device__ __forceinline__ RecCoef rec_coef(float lam, float sxv, int H)
+{
+    static_assert(kRecSeg == 32, "r^kRecSeg by five squarings");
+    const float a = fmaf(lam, sxv, 1.0f);                       // 1 + lam sx
+    const float d = fmaf(2.0f, lam, a);                         // 1 + lam sx + 2 lam
+    // r = (d - sqrt(d^2 - 4 lam^2)) / (2 lam), written without the cancellation
+    const float r = __fdiv_rn(2.0f * lam, d + sqrtf(a * fmaf(4.0f, lam, a)));
+    float rseg = r;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) rseg *= rseg;
+    const int nseg = (H + kRecSeg - 1) / kRecSeg;
+    const int last = H - (nseg - 1) * kRecSeg;
+    float rlast = 1.0f;
+    for (int k = 0; k < last; ++k) rlast *= r;
+    float rh = rlast;
+    for (int k = 1; k < nseg; ++k) rh *= rseg;
+    return RecCoef{r, rseg, rlast, __fdiv_rn(1.0f, 1.0f - rh)};
+}
+
+// Cyclic carries of one column from its segments' values from zero: forward (causal, carry into
+// segment s from the left) or backward (anticausal, from the right).
+template <bool BACKWARD>
+__device__ __forceinline__ void rec_carries(const RecCoef& k, int nseg, const float2* part,
+                                            float2* carry, int stride)
+{
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < nseg; ++q) {
+        const int sg = BACKWARD ? nseg - 1 - q : q;
+        const float rl = sg == nseg - 1 ? k.rlast : k.rseg;
+        const float2 p = part[sg * stride];
+        acc = make_float2(fmaf(rl, acc.x, p.x), fmaf(rl, acc.y, p.y));
+    }
+    float2 cin = make_float2(acc.x * k.icyc, acc.y * k.icyc);
+    for (int q = 0; q < nseg; ++q) {
+        const int sg = BACKWARD ? nseg - 1 - q : q;
+        carry[sg * stride] = cin;
+        const float rl = sg == nseg - 1 ? k.rlast : k.rseg;
+        const float2 p = part[sg * stride];
+        cin = make_float2(fmaf(rl, cin.x, p.x), fmaf(rl, cin.y, p.y));
+    }
+}
+
+// Shared memory of the recursion solve of one 32-column block: the segments' values and carries.
+__host__ __device__ __forceinline__ size_t rec_smem(int H)
+{
+    return sizeof(float2) * 2 * 32 * (size_t)((H + kRecSeg - 1) / kRecSeg);
+}
+
+// Columns [32 blk, 32 blk + 32) of one channel's half spectrum, solved in place by the recursion:
+// lanes on adjacent columns (each row's 32 values are one 256-byte run), warps on segments.  The
+// values pass through global memory (L2) between the phases; `sm` holds rec_smem(H) bytes.
+__device__ __forceinline__ void k3_rec_item(float2* __restrict__ spec, int H, int W, int blk,
+                                            const float* __restrict__ sx, float lam, float scale,
+                                            float2* sm)
+{
+    const int Wh = W / 2 + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int kx = blk * 32 + lane;
+    const bool live = kx < Wh;
+    const int nseg = (H + kRecSeg - 1) / kRecSeg;
+    float2* part = sm;                             // [segment][lane]
+    float2* carry = sm + (size_t)nseg * 32;        // [segment][lane]
+    const RecCoef k = rec_coef(lam, __ldg(sx + min(kx, Wh - 1)), H);
+    const float r = k.r;
+    float2* col = spec + kx;
+    // causal pass from zero in every segment: w[n] = R[n] + r w[n-1]
+    for (int sg = warp; sg < nseg; sg += nw) {
+        const int n0 = sg * kRecSeg;
+        float2 v[kRecSeg];
+#pragma unroll
+        for (int t = 0; t < kRecSeg; ++t)
+            v[t] = (live && n0 + t < H) ? col[(size_t)(n0 + t) * Wh] : make_float2(0.f, 0.f);
+        float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < kRecSeg; ++t)
+            if (n0 + t < H) w = make_float2(fmaf(r, w.x, v[t].x), fmaf(r, w.y, v[t].y));
+        part[sg * 32 + lane] = w;
+    }
+    __syncthreads();
+    if (warp == 0) rec_carries<false>(k, nseg, part + lane, carry + lane, 32);
+    __syncthreads();
+    // complete the causal pass; anticausal pass from zero: z[n] = w[n] + r z[n+1], stored
+    for (int sg = warp; sg < nseg; sg += nw) {
+        const int n0 = sg * kRecSeg;
+        float2 v[kRecSeg];
+#pragma unroll
+        for (int t = 0; t < kRecSeg; ++t)
+            v[t] = (live && n0 + t < H) ? col[(size_t)(n0 + t) * Wh] : make_float2(0.f, 0.f);
+        const float2 cin = carry[sg * 32 + lane];
+        float2 p = make_float2(r * cin.x, r * cin.y);
+        float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < kRecSeg; ++t)
+            if (n0 + t < H) {
+                w = make_float2(fmaf(r, w.x, v[t].x), fmaf(r, w.y, v[t].y));
+                v[t] = make_float2(w.x + p.x, w.y + p.y);
+                p = make_float2(r * p.x, r * p.y);
+            }
+        float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = kRecSeg - 1; t >= 0; --t)
+            if (n0 + t < H) {
+                z = make_float2(fmaf(r, z.x, v[t].x), fmaf(r, z.y, v[t].y));
+                if (live) col[(size_t)(n0 + t) * Wh] = z;
+            }
+        part[sg * 32 + lane] = z;
+    }
+    __syncthreads();
+    if (warp == 0) rec_carries<true>(k, nseg, part + lane, carry + lane, 32);
+    __syncthreads();
+    // complete the anticausal pass: Z = r z times H / (H W)
+    const float m = r * (scale * (float)H);
+    for (int sg = warp; sg < nseg; sg += nw) {
+        const int n0 = sg * kRecSeg;
+        const float2 cin = carry[sg * 32 + lane];
+        float2 p = make_float2(r * cin.x, r * cin.y);
+#pragma unroll
+        for (int t = kRecSeg - 1; t >= 0; --t)
+            if (n0 + t < H) {
+                if (live) {
+                    const float2 z = col[(size_t)(n0 + t) * Wh];
+                    col[(size_t)(n0 + t) * Wh] = make_float2((z.x + p.x) * m, (z.y + p.y) * m);
+                }
+                p = make_float2(r * p.x, r * p.y);
+            }
+    }
+    __syncthreads();
+}
+
+// K3 by recursion for one channel: one 32-column block per CTA (grid-stride).
+__global__ void __launch_bounds__(512) k3_cols_rec(float2* __restrict__ spec, int H, int W,
+                                                   const float* __restrict__ sx, float lam,
+                                                   float scale)
+{
+    extern __shared__ float2 smem[];
+    const int nblk = (W / 2 + 1 + 31) / 32;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x)
+        k3_rec_item(spec, H, W, blk, sx, lam, scale, smem);
+}
+
 // K3 on one column block already in `data` (rows n < H; the caller synchronised): forward FFT
 // down the columns, spectral divide (Eq. 8 denominator, F(1) = 1, with lam and the 1/(HW) of the
 // inverse), inverse FFT.  Ends synchronised.
@@ -869,8 +1028,12 @@ __global__ void __launch_bounds__(512) k3_batch(const BatchJob* __restrict__ job
         const int nblk = (Wh + (1 << J.lgc) - 1) >> J.lgc;
         const int local = item - __ldg(&grp[g].y);
         const int c = local / nblk, blk = local - c * nblk;
-        k3_item(J.spec + c * (size_t)J.H * Wh, J.H, J.W, blk, J.cp, J.rp.lap, J.cp.lap, J.lam,
-                J.scale, J.lgc, J.cp.tw, smem);
+        if (J.rec)   // 32-column blocks (lgc = 5) solved by the recursion
+            k3_rec_item(J.spec + c * (size_t)J.H * Wh, J.H, J.W, blk, J.rp.lap, J.lam, J.scale,
+                        smem);
+        else
+            k3_item(J.spec + c * (size_t)J.H * Wh, J.H, J.W, blk, J.cp, J.rp.lap, J.cp.lap, J.lam,
+                    J.scale, J.lgc, J.cp.tw, smem);
     }
 }
 
@@ -1203,6 +1366,7 @@ static void set_staged_attributes()
     for (int nc : kFusedBlocks)
         for (ColsFusedFn f : {cols_fused_kernel_p<ColPlanA>(nc), cols_fused_kernel_p<ColPlanB>(nc)})
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k3_cols_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // Block size of a column driver (fn: its kernel); see the comment above.
@@ -1225,6 +1389,8 @@ static int col_threads(const void* fn, const FftPlanDev& cp, int ncol, size_t sm
     *occ_out = best_occ;
     return best_t;
 }
+
+size_t solve_rec_smem(int H) { return rec_smem(H); }
 
 int solve_effective_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms)
 {
@@ -1276,7 +1442,13 @@ cudaError_t launch_solve_residual(const float* f, const float* ex, const float* 
         k2_rows_forward<<<grid_r, thr_r, smem_r, s>>>(ex, ey, spec, H, W, rp, tw_r);
     }
     if (marks) cudaEventRecord(marks[0], s);
-    if (cols_fused) {
+    if (cp.bluestein && p.lambda <= kRecLamMax) {
+        const int nb = (W / 2 + 1 + 31) / 32;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_cols_rec, 512, rec_smem(H));
+        const int grid = std::max(1, std::min(nb, num_sms * std::max(occ, 1)));
+        k3_cols_rec<<<grid, 512, rec_smem(H), s>>>(spec, H, W, sx, p.lambda, scale);
+    } else if (cols_fused) {
         const size_t sm3 = k3f_smem(cp.L, nc);
         int occ = 0;
         const int thr = col_threads((const void*)k3f, cp, nc, sm3, &occ);

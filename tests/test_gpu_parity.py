@@ -78,6 +78,24 @@ def test_solve_residual_matches_eq8(h, H, W, lam):
         assert np.array_equal(got, f)
 
 
+@pytest.mark.parametrize("H,W", [(211, 128), (1523, 96), (97, 300)])
+@pytest.mark.parametrize("lam", [0.5, 1.0e4, 2.0e4])
+def test_solve_recursion_columns_match_eq8(h, H, W, lam):
+    """Column lengths without a mixed-radix plan: up to lambda = 1e4 the column transform, divide
+    and inverse are the cyclic recursion they equal (its rounding grows like sqrt(lambda), largest
+    at 1e4), above it Bluestein transforms; both match Eq. 8, with more than one 32-column block
+    and a ragged last block (W = 300: 151 columns)."""
+    rng = np.random.default_rng(H + 7 * W)
+    f = rng.uniform(size=(H, W)).astype(np.float32)
+    ex = rng.normal(scale=0.05, size=(H, W)).astype(np.float32)
+    ey = rng.normal(scale=0.05, size=(H, W)).astype(np.float32)
+    got = solve_residual(h, f, ex, ey, lam)[0]
+    gx, gy = oracle.gradients(f)
+    want = oracle.solve_eq8(f, gx + ex.astype(np.float64), gy + ey.astype(np.float64), lam)
+    err = maxabs(got, want)
+    assert err <= TOL_FP32, err
+
+
 @pytest.mark.parametrize("H,W,log2_len", [(2160, 96, 12), (1080, 70, 11), (8, 3840, 3),
                                           (9, 1920, 4)])
 def test_solve_compile_time_plans_every_column_block(tmp_path, H, W, log2_len):
