@@ -65,6 +65,10 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--tune-table", default=None,
+                    help="launch-shape table: loaded if the file exists (no autotuning), else "
+                         "written by the autotuner (so a profiled run can take the shapes of a "
+                         "plain one)")
     return ap.parse_args()
 
 
@@ -210,16 +214,17 @@ def run_reference(args):
     return 0
 
 
-def bench_batched(h, dev, stream, flush, steps):
+def bench_batched(h, dev, stream, flush, steps, table=None, tuned=False):
     """64 uneven jobs (sizes log-uniform, C in {1,3}, per-job lambda, sigma_r, radius): one
     blfls_smooth_batch call (graph-replayed) vs. a loop of blfls_smooth calls, both timed with
     events after an L2 flush."""
     import torch
     from paper_1812_07122_gb300 import blfls, synth
     jobs = synth.batch_jobs(64, seed=4)
-    for r in sorted({j.radius for j in jobs}):
-        for prec in (0, 1):
-            blfls.blfls_autotune(h, 768, 1024, 1, r, prec, None)
+    if not tuned:   # shapes for the batch's radii (a loaded table already holds them)
+        for r in sorted({j.radius for j in jobs}):
+            for prec in (0, 1):
+                blfls.blfls_autotune(h, 768, 1024, 1, r, prec, table)
     xs, ys, cj, cj16 = [], [], [], []
     for j in jobs:
         x = torch.from_numpy(synth.job_image(j)).to(dev)
@@ -403,7 +408,8 @@ def main():
     x = torch.from_numpy(f).to(dev)
     out = torch.empty_like(x)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    h = blfls.blfls_create(local)
+    tuned_from_file = bool(args.tune_table) and os.path.exists(args.tune_table)
+    h = blfls.blfls_create(local, 0, args.tune_table if tuned_from_file else None)
     stream = torch.cuda.current_stream(dev)
     p = PARAMS
 
@@ -413,8 +419,10 @@ def main():
 
     # launch shapes for this workload from the project autotuner (K1 tile height per precision,
     # K3 column block), untimed; they change speed only, never results
-    for prec in (0, 1, 2):
-        blfls.blfls_autotune(h, H, W, 1, p["radius"], prec, None)
+    table = args.tune_table or os.path.join(tempfile.mkdtemp(), "tune.json")
+    if not tuned_from_file:
+        for prec in (0, 1, 2):
+            blfls.blfls_autotune(h, H, W, 1, p["radius"], prec, table)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
@@ -582,7 +590,7 @@ def main():
 
     batched = None
     if not args.no_batch:
-        batched = bench_batched(h, dev, stream, flush, K)
+        batched = bench_batched(h, dev, stream, flush, K, table, tuned_from_file)
     serving = None
     if not args.no_serve and rank == 0:
         serving = bench_serving(dev, args.serve_requests, args.serve_rate)
@@ -646,6 +654,10 @@ def main():
                                  "one_core_mp_per_s": round(0.065536 / c1_one, 4)}
 
     blfls.blfls_destroy(h)
+    try:
+        tuned = json.load(open(table))
+    except (OSError, ValueError):
+        tuned = None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "MP/s", "n_gpus": world,
                 "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -655,7 +667,10 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write)"},
                 "step_ms": step_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * K, "clocks": clocks, "forms": forms,
+                "gpu_launches": launches_per_step * K, "clocks": clocks,
+                "launch_shapes": {"source": "file" if tuned_from_file else "autotuner",
+                                  "table": tuned},
+                "forms": forms,
                 "modes": modes, "small": small, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
