@@ -332,8 +332,8 @@ def bench_serving(dev, n_req, rate):
 
 
 def hbm_peak_gbs():
-    """(peak GB/s, basis): the measured copy bandwidth of the GB300s when the driver has
-    written it, else the fallback figure."""
+    """(peak GB/s, basis): the measured HBM copy bandwidth recorded in MEASURED_PEAKS.json when
+    that file is present, else the fallback figure."""
     try:
         rec = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         return float(rec["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"

@@ -150,7 +150,7 @@ struct SolveParams {
 
 // Shared memory of the recursion K3 (kRecSeg) on a 32-column block of columns of length H.
 size_t solve_rec_smem(int H);
-// The K3 column block a solve launch takes for a requested col_block (0: the driver's own
+// The K3 column block a solve launch takes for a requested col_block (0: the column driver's own
 // choice) with column plan cp on an image W wide.
 int solve_effective_col_block(const FftPlanDev& cp, int W, int col_block, int num_sms);
 
