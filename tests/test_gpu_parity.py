@@ -100,8 +100,8 @@ def test_solve_recursion_columns_match_eq8(h, H, W, lam):
                                           (9, 1920, 4)])
 def test_solve_compile_time_plans_every_column_block(tmp_path, H, W, log2_len):
     """The lengths with compile-time plans (columns of 2160 and 1080, rows of 3840 and 1920),
-    with every column block the column driver can take (chosen through a tune table; 16
-    columns of 2160 points exceed the shared-memory budget and run as 13) and with the column driver's
+    with every column block the column driver can take (chosen through a tune table; 16 columns
+    of 2160 points exceed the shared-memory budget and run as 13) and with the column driver's
     own choice (an empty table): each matches Eq. 8, and all blocks give the same bits (a
     column's arithmetic does not depend on how columns are grouped)."""
     import json
