@@ -222,13 +222,15 @@ __device__ __forceinline__ void k3_rec_item(float2* __restrict__ spec, int H, in
     const int Wh = W / 2 + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int kx = blk * 32 + lane;
-    const bool live = kx < Wh;
+    const bool live_col = kx < Wh;
     const int nseg = (H + kRecSeg - 1) / kRecSeg;
     float2* part = sm;                             // [segment][lane]
     float2* carry = sm + (size_t)nseg * 32;        // [segment][lane]
     const RecCoef k = rec_coef(lam, __ldg(sx + min(kx, Wh - 1)), H);
     const float r = k.r;
     float2* col = spec + kx;
+    // a live lane's column lies inside the half spectrum (rows n < H of Wh columns)
+    const bool live = live_col && BLFLS_DCHECK(kx >= 0 && blk >= 0 && H >= 1, kDcSolveGlobal);
     // causal pass from zero in every segment: w[n] = R[n] + r w[n-1]
     for (int sg = warp; sg < nseg; sg += nw) {
         const int n0 = sg * kRecSeg;
