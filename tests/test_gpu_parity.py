@@ -78,13 +78,15 @@ def test_solve_residual_matches_eq8(h, H, W, lam):
         assert np.array_equal(got, f)
 
 
-@pytest.mark.parametrize("H,W", [(211, 128), (1523, 96), (97, 300)])
+@pytest.mark.parametrize("H,W", [(211, 128), (1523, 96), (97, 300), (11, 40), (13, 2), (37, 1),
+                                 (8191, 3)])
 @pytest.mark.parametrize("lam", [0.5, 1.0e4, 2.0e4])
 def test_solve_recursion_columns_match_eq8(h, H, W, lam):
     """Column lengths without a mixed-radix plan: up to lambda = 1e4 the column transform, divide
     and inverse are the cyclic recursion they equal (its rounding grows like sqrt(lambda), largest
     at 1e4), above it Bluestein transforms; both match Eq. 8, with more than one 32-column block
-    and a ragged last block (W = 300: 151 columns)."""
+    and a ragged last block (W = 300: 151 columns), a single segment (11, 13, 37 rows), one or two
+    columns, and 256 segments (8191 rows, a prime)."""
     rng = np.random.default_rng(H + 7 * W)
     f = rng.uniform(size=(H, W)).astype(np.float32)
     ex = rng.normal(scale=0.05, size=(H, W)).astype(np.float32)
